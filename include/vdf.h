@@ -1,0 +1,146 @@
+/*
+ * vdf.h -- C ABI of the GB300 directional vector filter library (libvdf.so).
+ *
+ * The library implements the order-statistics directional filters of
+ * M. E. Celebi, "Real-time implementation of order-statistics based
+ * directional filters":
+ *   - Section II: each pixel of an M x N RGB image is replaced by one member
+ *     of the sqrt(n) x sqrt(n) window centred on it (n = win * win), the
+ *     member that minimises an aggregated distance to all n members.
+ *   - BVDF, Eq. (2): aggregated angle  sum_j A(x_i, x_j),
+ *     A(x, y) = acos(<x,y> / (|x| |y|)).
+ *   - DDF, Eq. (3): (sum_j A)^p * (sum_j L2)^(1-p), L2 the Minkowski distance
+ *     of Eq. (1) at order 2; p = 1/2 orders like Eq. (3)'s plain product.
+ *   - Method 1 (Section 2.1, Eqs. (4)-(6), Table 1): A replaced by a degree-q
+ *     minimax polynomial.  Method 2 (Section 2.2, Eq. (7)): A replaced by the
+ *     chromaticity distance B; inside DDF B goes through Eq. (10) first.
+ *
+ * Conventions fixed by this library (the paper is silent):
+ *   - window members in raster order, index i = (dy+R)*win + (dx+R), centre
+ *     (n-1)/2; pixels outside the image are replaced by the nearest edge pixel;
+ *   - a zero vector is at angle pi/2 from every vector (cosine taken as 0) and
+ *     has chromaticity 0;
+ *   - DDF uses max(sum_j A, 0) inside the power and 0^0 = 1;
+ *   - ties: the centre if it attains the minimum, else the lowest index.
+ *
+ * Images are uint8, HWC (row-major, 3 bytes per pixel, row pitch 3*N bytes)
+ * unless stated.  Device pointers must come from the same CUDA context as
+ * the stream.  Every call is asynchronous on `stream` (a cudaStream_t, NULL
+ * for the legacy default stream) unless stated otherwise.  The library never
+ * allocates device memory inside these calls: scratch space is passed in as
+ * a caller-owned `workspace`.  Calls return VDF_OK (0) or a negative
+ * vdf_status; nothing throws or aborts across the ABI.
+ */
+#ifndef VDF_H
+#define VDF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum { VDF_BVDF = 0, VDF_DDF = 1 } vdf_filter_kind;
+
+/* Distance used in place of A (Section II; Methods 1 and 2). */
+typedef enum { VDF_DIST_EXACT = 0, VDF_DIST_MINIMAX = 1, VDF_DIST_RGB = 2 } vdf_dist_mode;
+
+/* VDF_PREC_FP64: every pair term, aggregate and comparison in double
+ * precision; ties are aggregates within 1e-11 (relative, floor 1e-3) of the
+ * minimum (in the log domain for DDF).
+ * VDF_PREC_FP32_RECHECK: single precision with a per-candidate certified
+ * error bound; a pixel whose minimum is not separated by the bounds, and
+ * whose near-minimal members are not provably equal (identical vectors, or
+ * collinear ones for BVDF, or exact zeros), is recomputed by the FP64 path.
+ * Both precisions therefore select the same member on every pixel. */
+typedef enum { VDF_PREC_FP64 = 0, VDF_PREC_FP32_RECHECK = 1 } vdf_precision;
+
+typedef enum {
+    VDF_OK = 0,
+    VDF_E_INVALID = -1,     /* null pointer, bad size, bad win / p / q, aliasing */
+    VDF_E_CUDA = -2,        /* a CUDA launch or copy failed (see vdf_last_cuda_error) */
+    VDF_E_OVERFLOW = -3,    /* recheck list larger than the workspace allows */
+    VDF_E_TIMEOUT = -4,     /* a bounded device-side wait gave up */
+    VDF_E_WORKSPACE = -5,   /* workspace missing or smaller than required */
+    VDF_E_UNSUPPORTED = -6  /* valid request this build does not implement */
+} vdf_status;
+
+/* Human-readable text of a status code (static storage). */
+const char *vdf_strerror(int status);
+
+/* Text of the last CUDA error seen by this thread (static storage). */
+const char *vdf_last_cuda_error(void);
+
+/* Bytes of device workspace vdf_filter needs for an M x N image with the
+ * given precision (0 for VDF_PREC_FP64).  Returns 0 on invalid sizes. */
+size_t vdf_workspace_bytes(int M, int N, int precision);
+
+/*
+ * Filter one M x N uint8 HWC image on the device.
+ *   img        device, M*N*3 bytes.  Not modified.
+ *   out        device, M*N*3 bytes: the selected member's RGB.  Must not
+ *              overlap img.
+ *   index_out  device, M*N int8 (may be NULL): selected raster index 0..n-1.
+ *   agg_out    device, M*N*n*2 doubles (may be NULL; FP64 precision only):
+ *              per pixel and member i, sum_j A_ij then sum_j L2_ij (the
+ *              latter 0 for BVDF).  For Method 2 in DDF the first value is
+ *              1.436437 * sum_j B_ij + 0.027664 * n (Eq. (10)).
+ *   win        3 or 5.   filter: vdf_filter_kind.   p: DDF exponent, [0, 1].
+ *   dist_mode  vdf_dist_mode.  minimax_q: 2, 3 or 4 (used for MINIMAX only).
+ *   precision  vdf_precision.
+ *   workspace  device, vdf_workspace_bytes(M, N, precision) bytes, 256-byte
+ *              aligned (NULL allowed when that size is 0).  Its contents on
+ *              return are the recheck counters (see vdf_workspace_stats).
+ * Errors: VDF_E_INVALID, VDF_E_WORKSPACE, VDF_E_UNSUPPORTED, VDF_E_CUDA.
+ */
+int vdf_filter(const uint8_t *img, int M, int N, int win, int filter, double p, int dist_mode, int minimax_q,
+               int precision, uint8_t *out, int8_t *index_out, double *agg_out, void *workspace,
+               size_t workspace_bytes, void *stream);
+
+/*
+ * The two stages of vdf_filter with VDF_PREC_FP32_RECHECK, for callers that
+ * want to time or overlap them separately.  vdf_fp32_pass zeroes the recheck
+ * counters, runs the FP32 tile kernel (writing out / index_out for every
+ * pixel, provisional where the bounds do not separate the minimum) and
+ * appends those pixels to the list in `workspace`.  vdf_fp64_recheck then
+ * recomputes the listed pixels with the FP64 path (it reads the list length
+ * on the device; no host synchronisation).  Arguments as for vdf_filter.
+ */
+int vdf_fp32_pass(const uint8_t *img, int M, int N, int win, int filter, double p, int dist_mode, int minimax_q,
+                  uint8_t *out, int8_t *index_out, void *workspace, size_t workspace_bytes, void *stream);
+int vdf_fp64_recheck(const uint8_t *img, int M, int N, int win, int filter, double p, int dist_mode,
+                     int minimax_q, uint8_t *out, int8_t *index_out, void *workspace, size_t workspace_bytes,
+                     void *stream);
+
+/* Recheck counters of the last vdf_filter that used `workspace`: pixels
+ * re-evaluated in FP64 and a non-zero overflow flag.  Synchronises `stream`
+ * and copies 8 bytes to the host. */
+int vdf_workspace_stats(const void *workspace, int64_t *rechecked, int32_t *overflow, void *stream);
+
+/*
+ * Same as vdf_filter with host buffers: copies img (M*N*3 bytes, host) to
+ * the device, filters, copies out (M*N*3) and index_out (M*N, may be NULL)
+ * back, and waits for the stream.  dev_buffer is device scratch of
+ * vdf_host_buffer_bytes(M, N, precision) bytes holding the device copies and
+ * the workspace.  Host buffers should be pinned for full copy speed.
+ */
+size_t vdf_host_buffer_bytes(int M, int N, int precision);
+int vdf_filter_host(const uint8_t *img_host, int M, int N, int win, int filter, double p, int dist_mode,
+                    int minimax_q, int precision, uint8_t *out_host, int8_t *index_out_host, void *dev_buffer,
+                    size_t dev_buffer_bytes, void *stream);
+
+/*
+ * Diagnostic: the FP32 path's per-member log scores and certified error
+ * bounds, without selection.  fe_out: device, M*N*n*2 floats: f then E per
+ * member (BVDF: f is the aggregate; DDF: f = p log2 sum A + (1-p) log2 sum L2).
+ * The true score lies in [f - E, f + E].
+ */
+int vdf_debug_fp32_scores(const uint8_t *img, int M, int N, int win, int filter, double p, int dist_mode,
+                          int minimax_q, float *fe_out, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VDF_H */

@@ -1,0 +1,236 @@
+// vdf_api.cu -- the C ABI of libvdf (declared in include/vdf.h): argument
+// checks, workspace layout and the launch sequence of each call.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <mutex>
+
+#include "../../include/vdf.h"
+#include "vdf_dispatch.h"
+
+namespace {
+
+thread_local char g_last_cuda[256] = "no error";
+
+int cuda_fail(cudaError_t e)
+{
+    if (e == cudaSuccess) return VDF_OK;
+    strncpy(g_last_cuda, cudaGetErrorString(e), sizeof(g_last_cuda) - 1);
+    g_last_cuda[sizeof(g_last_cuda) - 1] = 0;
+    return VDF_E_CUDA;
+}
+
+// Workspace of the FP32 path: two counters, padding to 256 bytes, then one
+// int32 pixel id per pixel (the recheck list can never overflow).
+constexpr size_t kCtrBytes = 256;
+
+bool valid_common(int M, int N, int win, int filter, double p, int dist, int q, int prec)
+{
+    if (M < 1 || N < 1 || (long long)M * N > (1LL << 31) - 1) return false;
+    if (win != 3 && win != 5) return false;
+    if (filter != VDF_BVDF && filter != VDF_DDF) return false;
+    if (filter == VDF_DDF && !(p >= 0.0 && p <= 1.0)) return false;
+    if (dist < VDF_DIST_EXACT || dist > VDF_DIST_RGB) return false;
+    if (dist == VDF_DIST_MINIMAX && (q < 2 || q > 4)) return false;
+    if (prec != VDF_PREC_FP64 && prec != VDF_PREC_FP32_RECHECK) return false;
+    return true;
+}
+
+bool overlaps(const void *a, size_t na, const void *b, size_t nb)
+{
+    const uintptr_t x = (uintptr_t)a, y = (uintptr_t)b;
+    return x < y + nb && y < x + na;
+}
+
+int num_sms()
+{
+    static int sms = 0;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 1;
+    });
+    return sms;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *vdf_strerror(int status)
+{
+    switch (status) {
+    case VDF_OK: return "ok";
+    case VDF_E_INVALID: return "invalid argument";
+    case VDF_E_CUDA: return "CUDA error";
+    case VDF_E_OVERFLOW: return "recheck list overflow";
+    case VDF_E_TIMEOUT: return "device-side wait timed out";
+    case VDF_E_WORKSPACE: return "workspace missing or too small";
+    case VDF_E_UNSUPPORTED: return "unsupported configuration";
+    default: return "unknown status";
+    }
+}
+
+const char *vdf_last_cuda_error(void) { return g_last_cuda; }
+
+size_t vdf_workspace_bytes(int M, int N, int precision)
+{
+    if (M < 1 || N < 1) return 0;
+    if (precision != VDF_PREC_FP32_RECHECK) return 0;
+    return kCtrBytes + sizeof(int) * (size_t)M * (size_t)N;
+}
+
+static int check_filter_args(const uint8_t *img, int M, int N, int win, int filter, double p, int dist_mode,
+                             int minimax_q, int precision, const uint8_t *out, const int8_t *index_out,
+                             const double *agg_out, const void *workspace, size_t workspace_bytes)
+{
+    if (!img || !out || !valid_common(M, N, win, filter, p, dist_mode, minimax_q, precision)) return VDF_E_INVALID;
+    const size_t bytes = (size_t)M * N * 3;
+    if (overlaps(img, bytes, out, bytes)) return VDF_E_INVALID;
+    if (index_out && (overlaps(index_out, (size_t)M * N, img, bytes) || overlaps(index_out, (size_t)M * N, out, bytes)))
+        return VDF_E_INVALID;
+    if (agg_out && precision != VDF_PREC_FP64) return VDF_E_INVALID;
+    const size_t need = vdf_workspace_bytes(M, N, precision);
+    if (need && (!workspace || workspace_bytes < need || ((uintptr_t)workspace & 255))) return VDF_E_WORKSPACE;
+    return VDF_OK;
+}
+
+static vdf::TileParams tile_params(const uint8_t *img, int M, int N, double p, int q, uint8_t *out, int8_t *idx,
+                                   double *agg, void *workspace)
+{
+    vdf::TileParams prm{};
+    prm.img = img;
+    prm.out = out;
+    prm.idx = idx;
+    prm.agg = agg;
+    prm.M = M;
+    prm.N = N;
+    prm.B = 1;
+    prm.p = p;
+    prm.q = q;
+    if (workspace) {
+        prm.recheck_ctr = (unsigned *)workspace;
+        prm.recheck_list = (int *)((char *)workspace + kCtrBytes);
+        prm.recheck_cap = (unsigned)((size_t)M * N);
+    }
+    return prm;
+}
+
+int vdf_fp32_pass(const uint8_t *img, int M, int N, int win, int filter, double p, int dist_mode, int minimax_q,
+                  uint8_t *out, int8_t *index_out, void *workspace, size_t workspace_bytes, void *stream)
+{
+    int rc = check_filter_args(img, M, N, win, filter, p, dist_mode, minimax_q, VDF_PREC_FP32_RECHECK, out,
+                               index_out, nullptr, workspace, workspace_bytes);
+    if (rc != VDF_OK) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    const vdf::TileParams prm = tile_params(img, M, N, p, minimax_q, out, index_out, nullptr, workspace);
+    cudaError_t e = cudaMemsetAsync(prm.recheck_ctr, 0, 2 * sizeof(unsigned), st);
+    if (e == cudaSuccess) e = vdf::run_fp32(prm, win / 2, filter, dist_mode, st);
+    return cuda_fail(e);
+}
+
+int vdf_fp64_recheck(const uint8_t *img, int M, int N, int win, int filter, double p, int dist_mode,
+                     int minimax_q, uint8_t *out, int8_t *index_out, void *workspace, size_t workspace_bytes,
+                     void *stream)
+{
+    int rc = check_filter_args(img, M, N, win, filter, p, dist_mode, minimax_q, VDF_PREC_FP32_RECHECK, out,
+                               index_out, nullptr, workspace, workspace_bytes);
+    if (rc != VDF_OK) return rc;
+    vdf::RecheckParams rp{};
+    rp.img = img;
+    rp.out = out;
+    rp.idx = index_out;
+    rp.list = (const int *)((const char *)workspace + kCtrBytes);
+    rp.ctr = (const unsigned *)workspace;
+    rp.cap = (unsigned)((size_t)M * N);
+    rp.M = M;
+    rp.N = N;
+    rp.p = p;
+    rp.q = minimax_q;
+    return cuda_fail(vdf::run_recheck(rp, win / 2, filter, dist_mode, num_sms() * 4, (cudaStream_t)stream));
+}
+
+int vdf_filter(const uint8_t *img, int M, int N, int win, int filter, double p, int dist_mode, int minimax_q,
+               int precision, uint8_t *out, int8_t *index_out, double *agg_out, void *workspace,
+               size_t workspace_bytes, void *stream)
+{
+    int rc = check_filter_args(img, M, N, win, filter, p, dist_mode, minimax_q, precision, out, index_out, agg_out,
+                               workspace, workspace_bytes);
+    if (rc != VDF_OK) return rc;
+    if (precision == VDF_PREC_FP64) {
+        const vdf::TileParams prm = tile_params(img, M, N, p, minimax_q, out, index_out, agg_out, nullptr);
+        return cuda_fail(vdf::run_fp64(prm, win / 2, filter, dist_mode, false, (cudaStream_t)stream));
+    }
+    rc = vdf_fp32_pass(img, M, N, win, filter, p, dist_mode, minimax_q, out, index_out, workspace, workspace_bytes,
+                       stream);
+    if (rc != VDF_OK) return rc;
+    return vdf_fp64_recheck(img, M, N, win, filter, p, dist_mode, minimax_q, out, index_out, workspace,
+                            workspace_bytes, stream);
+}
+
+int vdf_workspace_stats(const void *workspace, int64_t *rechecked, int32_t *overflow, void *stream)
+{
+    if (!workspace) return VDF_E_INVALID;
+    unsigned h[2] = {0, 0};
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(h, workspace, sizeof(h), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e);
+    if (rechecked) *rechecked = h[0];
+    if (overflow) *overflow = (int32_t)h[1];
+    return VDF_OK;
+}
+
+size_t vdf_host_buffer_bytes(int M, int N, int precision)
+{
+    if (M < 1 || N < 1) return 0;
+    const size_t px = (size_t)M * N;
+    auto up = [](size_t v) { return (v + 255) & ~(size_t)255; };
+    return up(3 * px) + up(3 * px) + up(px) + vdf_workspace_bytes(M, N, precision);
+}
+
+int vdf_filter_host(const uint8_t *img_host, int M, int N, int win, int filter, double p, int dist_mode,
+                    int minimax_q, int precision, uint8_t *out_host, int8_t *index_out_host, void *dev_buffer,
+                    size_t dev_buffer_bytes, void *stream)
+{
+    if (!img_host || !out_host || !dev_buffer || M < 1 || N < 1) return VDF_E_INVALID;
+    const size_t need = vdf_host_buffer_bytes(M, N, precision);
+    if (dev_buffer_bytes < need || ((uintptr_t)dev_buffer & 255)) return VDF_E_WORKSPACE;
+    const size_t px = (size_t)M * N;
+    auto up = [](size_t v) { return (v + 255) & ~(size_t)255; };
+    uint8_t *d_in = (uint8_t *)dev_buffer;
+    uint8_t *d_out = d_in + up(3 * px);
+    int8_t *d_idx = (int8_t *)(d_out + up(3 * px));
+    void *ws = (char *)d_idx + up(px);
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(d_in, img_host, 3 * px, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e);
+    int rc = vdf_filter(d_in, M, N, win, filter, p, dist_mode, minimax_q, precision, d_out,
+                        index_out_host ? d_idx : nullptr, nullptr, ws, vdf_workspace_bytes(M, N, precision), stream);
+    if (rc != VDF_OK) return rc;
+    e = cudaMemcpyAsync(out_host, d_out, 3 * px, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && index_out_host) e = cudaMemcpyAsync(index_out_host, d_idx, px, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    return cuda_fail(e);
+}
+
+int vdf_debug_fp32_scores(const uint8_t *img, int M, int N, int win, int filter, double p, int dist_mode,
+                          int minimax_q, float *fe_out, void *stream)
+{
+    if (!img || !fe_out || !valid_common(M, N, win, filter, p, dist_mode, minimax_q, VDF_PREC_FP32_RECHECK))
+        return VDF_E_INVALID;
+    vdf::TileParams prm{};
+    prm.img = img;
+    prm.dbg_fe = fe_out;
+    prm.M = M;
+    prm.N = N;
+    prm.B = 1;
+    prm.p = p;
+    prm.q = minimax_q;
+    return cuda_fail(vdf::run_fp32(prm, win / 2, filter, dist_mode, (cudaStream_t)stream));
+}
+
+}  // extern "C"

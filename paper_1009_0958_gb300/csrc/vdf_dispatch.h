@@ -1,0 +1,18 @@
+// vdf_dispatch.h -- internal entry points between the C ABI (vdf_api.cu) and
+// the kernel instantiation units (vdf_fp64.cu, vdf_fp32.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "vdf_tile.cuh"
+
+namespace vdf {
+
+// FP64 tile kernel (uint8 input, or float32 NCHW input when f32in).
+cudaError_t run_fp64(const TileParams &prm, int R, int filter, int dist, bool f32in, cudaStream_t st);
+// FP32 certified tile kernel (uint8 input).
+cudaError_t run_fp32(const TileParams &prm, int R, int filter, int dist, cudaStream_t st);
+// FP64 recheck of the pixels listed by run_fp32.
+cudaError_t run_recheck(const RecheckParams &prm, int R, int filter, int dist, int blocks, cudaStream_t st);
+
+}  // namespace vdf

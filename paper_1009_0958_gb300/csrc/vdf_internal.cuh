@@ -1,0 +1,254 @@
+// vdf_internal.cuh -- pair terms, constants and selection rules shared by the
+// CUDA kernels of libvdf (not part of the public ABI).
+//
+// Paper: M. E. Celebi, "Real-time implementation of order-statistics based
+// directional filters".  Section II defines the filters (Eqs. (1)-(3)),
+// Section 2.1 Method 1 (Eqs. (4)-(6), Table 1), Section 2.2 Method 2
+// (Eq. (7)); Section 3.2 gives the linear map of Eq. (10).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+namespace vdf {
+
+enum Filter { BVDF = 0, DDF = 1 };
+enum Dist { EXACT = 0, MINIMAX = 1, RGB = 2 };
+
+// ------------------------------------------------------------- constants --
+
+// Table 1, Section 2.1: minimax coefficients a_0..a_q for q = 2, 3, 4, padded
+// with zeros to degree 4 (a zero leading coefficient leaves Horner's rule
+// bit-identical).  ASIN rows are polynomials in tau = sqrt(1 - z) used for
+// z >= 1/2 (Eq. (6)); ACOS rows are polynomials in z used for z < 1/2.
+static __constant__ double kAsin64[3][5] = {
+    {1.829125e-03, 1.371117, 1.480266e-01, 0.0, 0.0},
+    {-1.358425e-04, 1.419488, -3.090315e-02, 1.666491e-01, 0.0},
+    {2.097797e-05, 1.412840, 1.429881e-02, 6.704361e-02, 6.909677e-02},
+};
+static __constant__ double kAcos64[3][5] = {
+    {1.569882, -9.695260e-01, -1.480266e-01, 0.0, 0.0},
+    {1.570864, -1.003730, 3.090318e-02, -2.356775e-01, 0.0},
+    {1.570786, -9.990285e-01, -1.429899e-02, -9.481335e-02, -1.381942e-01},
+};
+static __constant__ float kAsin32[3][5] = {
+    {1.829125e-03f, 1.371117f, 1.480266e-01f, 0.0f, 0.0f},
+    {-1.358425e-04f, 1.419488f, -3.090315e-02f, 1.666491e-01f, 0.0f},
+    {2.097797e-05f, 1.412840f, 1.429881e-02f, 6.704361e-02f, 6.909677e-02f},
+};
+static __constant__ float kAcos32[3][5] = {
+    {1.569882f, -9.695260e-01f, -1.480266e-01f, 0.0f, 0.0f},
+    {1.570864f, -1.003730f, 3.090318e-02f, -2.356775e-01f, 0.0f},
+    {1.570786f, -9.990285e-01f, -1.429899e-02f, -9.481335e-02f, -1.381942e-01f},
+};
+
+// Eq. (10): A ~ 1.436437 B + 0.027664.
+constexpr double kSlope64 = 1.436437;
+constexpr double kOffset64 = 0.027664;
+constexpr float kSlope32 = 1.436437f;
+constexpr float kOffset32 = 0.027664f;
+
+constexpr double kHalfPi64 = 1.5707963267948966;   // nearest double to pi/2
+constexpr float kHalfPi32 = 1.57079637f;           // nearest float to pi/2
+
+// atan(t) = t * Q(t^2) on [0, 1]: minimax fit for relative error (script
+// gen_atan_poly.py next to this file); float32 Horner evaluation error is
+// below 3.6 ulp of the result over the whole range.
+static __constant__ float kAtanQ[8] = {0.99999988f, -0.3333199f,    0.19969724f,  -0.14019482f,
+                                     0.099142946f, -0.059486423f, 0.02425243f,  -0.0046932846f};
+
+// ----------------------------------------------------- FP64 pair terms ----
+// Inputs are the integer RGB values of two pixels with n2 = |x|^2 in .w.
+// Every integer intermediate is exact; each term is a symmetric function of
+// its two arguments, bit for bit.
+
+__device__ __forceinline__ double horner4_64(const double *a, double t)
+{
+    double v = a[4];
+    v = __fma_rn(v, t, a[3]);
+    v = __fma_rn(v, t, a[2]);
+    v = __fma_rn(v, t, a[1]);
+    v = __fma_rn(v, t, a[0]);
+    return v;
+}
+
+// Angular term of the distance mode (BVDF form; for DDF with Method 2 the
+// caller applies Eq. (10) to the aggregate).
+template <int DIST>
+__device__ __forceinline__ double aterm64(const int4 a, const int4 b, int q)
+{
+    const int d = a.x * b.x + a.y * b.y + a.z * b.z;
+    const long long P = (long long)a.w * (long long)b.w;
+    if (DIST == EXACT) {
+        // Eq. (2): acos(<x,y>/(|x||y|)) = atan2(|x cross y|, <x,y>) for <x,y> >= 0,
+        // with |x cross y|^2 = |x|^2 |y|^2 - <x,y>^2 (Lagrange) exact in int64.
+        if (P == 0) return kHalfPi64;
+        const long long c2 = P - (long long)d * d;
+        return atan2(sqrt((double)c2), (double)d);
+    } else if (DIST == MINIMAX) {
+        // Eqs. (4)-(6): branch on z >= 1/2, i.e. 4 <x,y>^2 >= |x|^2 |y|^2 (exact).
+        if (P != 0 && 4LL * d * d >= P) {
+            const long long c2 = P - (long long)d * d;
+            const double s = sqrt((double)P);
+            // 1 - z = |x cross y|^2 / (s (s + <x,y>)), s = |x||y|
+            const double t = sqrt((double)c2 / (s * (s + (double)d)));
+            return horner4_64(kAsin64[q - 2], t);
+        }
+        const double z = (P == 0) ? 0.0 : (double)d / sqrt((double)P);
+        return horner4_64(kAcos64[q - 2], z);
+    } else {
+        // Eq. (7): L2 of the chromaticities, sqrt(sum_k (s_y x_k - s_x y_k)^2) / (s_x s_y).
+        const int sa = a.x + a.y + a.z, sb = b.x + b.y + b.z;
+        if (sa == 0 || sb == 0) {
+            if (sa == 0 && sb == 0) return 0.0;
+            return sa == 0 ? sqrt((double)b.w) / (double)sb : sqrt((double)a.w) / (double)sa;
+        }
+        const long long t0 = (long long)sb * a.x - (long long)sa * b.x;
+        const long long t1 = (long long)sb * a.y - (long long)sa * b.y;
+        const long long t2 = (long long)sb * a.z - (long long)sa * b.z;
+        const long long N = t0 * t0 + t1 * t1 + t2 * t2;
+        return sqrt((double)N) / ((double)sa * (double)sb);
+    }
+}
+
+// Eq. (1) at order 2.
+__device__ __forceinline__ double l2term64(const int4 a, const int4 b)
+{
+    const int d = a.x * b.x + a.y * b.y + a.z * b.z;
+    return sqrt((double)(a.w + b.w - 2 * d));
+}
+
+// FP64 terms for float32 inputs (exact mode only): products of two float32
+// values are exact in double; each cross-product component is rounded once.
+__device__ __forceinline__ double aterm64f(const float4 a, const float4 b)
+{
+    const double ax = a.x, ay = a.y, az = a.z, bx = b.x, by = b.y, bz = b.z;
+    const double na = __dadd_rn(__dadd_rn(__dmul_rn(ax, ax), __dmul_rn(ay, ay)), __dmul_rn(az, az));
+    const double nb = __dadd_rn(__dadd_rn(__dmul_rn(bx, bx), __dmul_rn(by, by)), __dmul_rn(bz, bz));
+    if (na == 0.0 || nb == 0.0) return kHalfPi64;
+    const double d = __dadd_rn(__dadd_rn(__dmul_rn(ax, bx), __dmul_rn(ay, by)), __dmul_rn(az, bz));
+    const double c0 = __fma_rn(ay, bz, -__dmul_rn(az, by));
+    const double c1 = __fma_rn(az, bx, -__dmul_rn(ax, bz));
+    const double c2 = __fma_rn(ax, by, -__dmul_rn(ay, bx));
+    const double cc = __dadd_rn(__dadd_rn(__dmul_rn(c0, c0), __dmul_rn(c1, c1)), __dmul_rn(c2, c2));
+    return atan2(sqrt(cc), d);
+}
+
+__device__ __forceinline__ double l2term64f(const float4 a, const float4 b)
+{
+    const double e0 = (double)a.x - (double)b.x, e1 = (double)a.y - (double)b.y, e2 = (double)a.z - (double)b.z;
+    return sqrt(__dadd_rn(__dadd_rn(__dmul_rn(e0, e0), __dmul_rn(e1, e1)), __dmul_rn(e2, e2)));
+}
+
+// ----------------------------------------------------- FP32 pair terms ----
+// Inputs: float4 {x, y, z, |x|^2} of integer-valued pixels (all exact in
+// float32), plus per-pixel auxiliaries for Methods 1 and 2.  Each term comes
+// with a relative (or, for Method 1, absolute) error bound used by the
+// certification in select32(); the bounds are derived in the design notes.
+
+constexpr float kU = 5.9604645e-08f;   // 2^-24
+
+struct Aux {
+    float a, b;   // Method 1: |x|, 1/|x| (0 for a zero vector); Method 2: sum x_k, |x|/sum x_k
+};
+
+// Exact integer products split into hi + lo parts (Dekker via FMA):
+// P = |x|^2 |y|^2 and D = <x,y>^2, then c2 = P - D with one rounding.
+struct PairInts {
+    float d, Ph, Pl, Dh, Dl;
+};
+
+__device__ __forceinline__ PairInts pair_ints(const float4 a, const float4 b)
+{
+    PairInts r;
+    r.d = fmaf(a.z, b.z, fmaf(a.y, b.y, a.x * b.x));   // exact (< 2^24)
+    r.Ph = a.w * b.w;
+    r.Pl = fmaf(a.w, b.w, -r.Ph);
+    r.Dh = r.d * r.d;
+    r.Dl = fmaf(r.d, r.d, -r.Dh);
+    return r;
+}
+
+__device__ __forceinline__ float cross2_32(const PairInts &r)
+{
+    // (Ph - Dh) is exact when the two are within a factor 2 (Sterbenz), and
+    // (Pl - Dl) is a difference of small exact integers; the result has one
+    // rounding, i.e. relative error <= u (<= 2u when the angle exceeds 45 deg).
+    return (r.Ph - r.Dh) + (r.Pl - r.Dl);
+}
+
+// Eq. (2) angle in FP32: theta = atan2(sqrt(c2), d) via t = min(tan, cot).
+// Relative error <= 16u (rsqrt 2 ulp, the Lagrange c2, the polynomial).
+__device__ __forceinline__ float angle32(const PairInts &r)
+{
+    const float c2 = cross2_32(r);
+    const float m = fmaxf(c2 * r.Dh, 1e-30f);
+    const float rs = rsqrtf(m);
+    const float ta = c2 * rs;     // sqrt(c2)/d = tan(theta)
+    const float tb = r.Dh * rs;   // d/sqrt(c2) = cot(theta)
+    const float t = fminf(ta, tb);
+    const float s = t * t;
+    float v = kAtanQ[7];
+#pragma unroll
+    for (int k = 6; k >= 0; --k) v = fmaf(v, s, kAtanQ[k]);
+    const float a = t * v;
+    // ta >= tb: theta >= 45 deg (also a zero vector: both 0, theta = pi/2)
+    return (ta >= tb) ? (kHalfPi32 - a) : a;
+}
+
+__device__ __forceinline__ float l2term32(const float4 a, const float4 b, float d)
+{
+    const float e = fmaf(-2.0f, d, a.w + b.w);   // |x - y|^2, exact
+    return e * rsqrtf(fmaxf(e, 1e-30f));          // relative error <= 5u
+}
+
+__device__ __forceinline__ float horner4_32(const float *c, float t)
+{
+    float v = c[4];
+    v = fmaf(v, t, c[3]);
+    v = fmaf(v, t, c[2]);
+    v = fmaf(v, t, c[1]);
+    v = fmaf(v, t, c[0]);
+    return v;
+}
+
+// Method 1 in FP32.  The branch z >= 1/2 is decided exactly:
+// 4<x,y>^2 - |x|^2|y|^2 = (4Dh - Ph) + (4Dl - Pl) keeps its sign.
+// Absolute error <= 24u.
+__device__ __forceinline__ float minimax32(const PairInts &r, const Aux xa, const Aux xb, int q)
+{
+    const float v = (4.0f * r.Dh - r.Ph) + (4.0f * r.Dl - r.Pl);
+    const bool upper = (v >= 0.0f) && (r.Ph > 0.0f);
+    const float c2 = cross2_32(r);
+    const float np = xa.a * xb.a;                              // |x||y|
+    const float tau = c2 * rsqrtf(fmaxf(c2 * np * (np + r.d), 1e-30f));   // sqrt(1 - z)
+    const float z = r.d * xa.b * xb.b;                         // 0 for a zero vector
+    return upper ? horner4_32(kAsin32[q - 2], tau) : horner4_32(kAcos32[q - 2], z);
+}
+
+// Method 2 in FP32: B = sqrt(N) / (s_x s_y), N from exact integer differences.
+// Relative error <= 11u.
+__device__ __forceinline__ float chroma32(const float4 a, const float4 b, const Aux xa, const Aux xb)
+{
+    const float ss = xa.a * xb.a;   // exact (< 2^24)
+    const float t0 = fmaf(xb.a, a.x, -(xa.a * b.x));
+    const float t1 = fmaf(xb.a, a.y, -(xa.a * b.y));
+    const float t2 = fmaf(xb.a, a.z, -(xa.a * b.z));
+    const float N = fmaf(t2, t2, fmaf(t1, t1, t0 * t0));
+    const float D = ss * ss;
+    const float B = N * rsqrtf(fmaxf(N * D, 1e-30f));
+    return (ss == 0.0f) ? (xa.b + xb.b) : B;
+}
+
+// log2 with exact exponent extraction: |error| <= 2^-22.6 + u |result|.
+__device__ __forceinline__ float log2_rr(float x)
+{
+    if (!(x > 0.0f)) return -INFINITY;
+    const int bits = __float_as_int(x);
+    const int e = ((bits >> 23) & 0xff) - 127;
+    const float m = __int_as_float((bits & 0x007fffff) | 0x3f800000);   // [1, 2)
+    return (float)e + __log2f(m);
+}
+
+}  // namespace vdf

@@ -1,0 +1,599 @@
+// vdf_tile.cuh -- the tile kernel of the directional vector filters.
+//
+// One CTA filters a TW x TH tile of output pixels.  The candidate region C is
+// the tile plus an R-pixel halo (R = win/2): every member of every window of
+// the tile lies in C, and so does every pair partner that such a window
+// needs.  One thread owns one candidate pixel p of C and accumulates, for
+// each of the n windows W(q) that contain p (q = p - e, e in [-R,R]^2), the
+// aggregate sum_{j in W(q)} term(x_p, x_j) of Eqs. (2)/(3).
+//
+// Pair terms are computed once per unordered pair: the (2w-1)^2 - 1 offsets
+// between members of a common window are processed in 2R+1 slices of equal
+// vertical offset dy' = 0..2R.  In a slice, each p computes its terms with
+// the partners p + (dy', dx) and stores them in shared-memory planes; after a
+// barrier, p reads its own row (offset +dy') and the mirrored row (offset
+// -dy', written by the pixels above it), forms the horizontal window sums and
+// adds them into the n accumulators of the windows whose rows they belong to.
+//
+// After the slices every thread turns its n aggregates into scores and
+// scatters them to the windows (shared memory), and one thread per output
+// pixel selects the minimum (Section II: reduced ordering, argmin).
+//
+// Summation order (relied on by the FP64 recheck kernel, which reproduces it
+// bit for bit): a window row sum adds dx = -R-ex .. R-ex left to right; the
+// aggregate adds the row sums in the order dy = 0, +1, -1, +2, -2, ...
+#pragma once
+
+#include <type_traits>
+#include <utility>
+
+#include "vdf_internal.cuh"
+
+namespace vdf {
+
+struct TileParams {
+    const void *img;       // uint8 HWC, or float32 NCHW (batch)
+    void *out;             // same layout and type as img
+    int8_t *idx;           // M*N (per image), may be null
+    double *agg;           // FP64: M*N*n*2 aggregates, may be null
+    float *dbg_fe;         // FP32: M*N*n*2 (score, bound), may be null (diagnostic)
+    int *recheck_list;     // FP32: pixel ids needing the FP64 path
+    unsigned *recheck_ctr; // [0] = count, [1] = overflow flag
+    unsigned recheck_cap;
+    int M, N, B;
+    double p;
+    int q;
+};
+
+template <int R_, int FILTER_, int DIST_, bool FP64_, bool F32IN_, int TW_, int TH_>
+struct TileCfg {
+    static constexpr int R = R_, FILTER = FILTER_, DIST = DIST_, TW = TW_, TH = TH_;
+    static constexpr bool FP64 = FP64_, F32IN = F32IN_;
+    static constexpr int W = 2 * R + 1, NW = W * W, CENTRE = (NW - 1) / 2;
+    static constexpr int CW = TW + 2 * R, CH = TH + 2 * R, NC = CW * CH;
+    static constexpr int NT = (NC + 31) / 32 * 32;
+    static constexpr int PXW = CW + 4 * R;            // pixel columns -2R .. CW+2R-1 of C
+    static constexpr int PLW = CW + 4 * R;            // plane columns -2R .. CW+2R-1
+    static constexpr int PLH = CH + 2 * R;            // plane rows -2R .. CH-1
+    static constexpr int NPL = 4 * R + 1;             // planes per slice (dx = -2R..2R)
+    static constexpr bool AUX = !FP64 && (DIST != EXACT);
+    using Real = typename std::conditional<FP64, double, float>::type;
+    using Pix = typename std::conditional<FP64 && !F32IN, int4, float4>::type;
+    struct Term {
+        Real a, l;
+    };
+    using PlaneT = typename std::conditional<FILTER == DDF, Term, Real>::type;
+    using HwT = typename std::conditional<FP64, double, float2>::type;
+    static constexpr size_t PIX_BYTES = sizeof(Pix) * CH * PXW;
+    static constexpr size_t AUX_BYTES = AUX ? (sizeof(Aux) * CH * PXW + 15) / 16 * 16 : 0;
+    static constexpr size_t PLANE_BYTES = sizeof(PlaneT) * NPL * PLH * PLW;
+    static constexpr size_t HW_BYTES = sizeof(HwT) * TW * TH * NW;
+    static constexpr size_t UNION_BYTES = PLANE_BYTES > HW_BYTES ? PLANE_BYTES : HW_BYTES;
+    static constexpr size_t SMEM = PIX_BYTES + AUX_BYTES + UNION_BYTES;
+};
+
+// ------------------------------------------------------------ scores ------
+
+// FP64 score of one member from its aggregates (Eq. (2) / Eq. (3)).  DDF is
+// compared in the log domain: p ln(max(SA,0)) + (1-p) ln(SL), 0 ln 0 := 0.
+template <int FILTER>
+__device__ __forceinline__ double score64(double sa, double sl, double p)
+{
+    if (FILTER == BVDF) return sa;
+    double f = 0.0;
+    if (p > 0.0) f = __dmul_rn(p, log(sa > 0.0 ? sa : 0.0));
+    if (p < 1.0) f = __dadd_rn(f, __dmul_rn(1.0 - p, log(sl)));
+    return f;
+}
+
+// Member selection of the FP64 path: scores within 1e-11 of the minimum
+// (relative with floor 1e-3 for BVDF; absolute in the log domain for DDF)
+// are tied; the centre wins a tie, else the lowest index.
+template <int FILTER, int NW>
+__device__ __forceinline__ int select64(const double *f)
+{
+    double m = f[0];
+#pragma unroll
+    for (int k = 1; k < NW; ++k) m = fmin(m, f[k]);
+    const double tol = (FILTER == BVDF) ? 1e-11 * fmax(fabs(m), 1e-3) : 1e-11;
+    constexpr int c = (NW - 1) / 2;
+    if (f[c] == m || f[c] - m <= tol) return c;
+#pragma unroll
+    for (int k = 0; k < NW; ++k)
+        if (f[k] == m || f[k] - m <= tol) return k;
+    return c;   // not reached
+}
+
+// FP32 score and certified bound.  Relative error bounds (in units of
+// u = 2^-24) of the aggregates: angle 16 + 4R (terms + two summation
+// stages), chromaticity 11 + 4R (+2 for Eq. (10)), L2 6 + 4R; Method 1 has
+// an absolute bound 24u per term plus 4R u |SA|.  Bounds are doubled.
+template <int R, int FILTER, int DIST>
+__device__ __forceinline__ float2 score32(float sa, float sl, float p)
+{
+    constexpr int NW = (2 * R + 1) * (2 * R + 1);
+    constexpr float S = 4.0f * R;
+    constexpr float kSafety = 2.0f;
+    if (FILTER == BVDF) {
+        float E;
+        if (DIST == EXACT) E = (16.0f + S) * kU * sa;
+        else if (DIST == RGB) E = (11.0f + S) * kU * sa;
+        else E = 24.0f * NW * kU + S * kU * (fabsf(sa) + NW * 2e-4f);
+        return make_float2(sa, kSafety * E);
+    }
+    // DDF, log2 domain
+    float relA;
+    bool unsure = false;
+    if (DIST == EXACT) relA = (16.0f + S) * kU;
+    else if (DIST == RGB) relA = (13.0f + S) * kU;
+    else {
+        const float absA = 24.0f * NW * kU + S * kU * (fabsf(sa) + NW * 2e-4f);
+        unsure = (p > 0.0f) && (sa <= 2.0f * absA);
+        relA = absA / fmaxf(sa, 1e-30f);
+    }
+    if (unsure) return make_float2(-1e30f, INFINITY);   // Method 1 sum too close to 0 to take its log
+    const float relL = (6.0f + S) * kU;
+    constexpr float kLg2Abs = 1.6e-7f;   // __log2f on [1,2): 2^-22.6
+    constexpr float kInvLn2 = 1.4426950f;
+    float f = 0.0f, E = 0.0f, lsum = 0.0f;
+    if (p > 0.0f) {
+        const float l1 = log2_rr(fmaxf(sa, 0.0f));
+        f = p * l1;
+        E += p * relA * kInvLn2 + kLg2Abs + kU * fabsf(l1);
+        lsum += fabsf(l1);
+    }
+    if (p < 1.0f) {
+        const float l2 = log2_rr(sl);
+        f = fmaf(1.0f - p, l2, f);
+        E += (1.0f - p) * relL * kInvLn2 + kLg2Abs + kU * fabsf(l2);
+        lsum += fabsf(l2);
+    }
+    if (f == -INFINITY) return make_float2(f, 0.0f);   // an aggregate is exactly 0
+    E += 2.0f * kU * (fabsf(f) + lsum);                 // combine rounding, float p
+    return make_float2(f, kSafety * E);
+}
+
+// ---------------------------------------------------------- the kernel ----
+
+template <class C>
+__device__ __forceinline__ typename C::Pix load_pixel(const TileParams &prm, int b, int gy, int gx)
+{
+    gy = min(max(gy, 0), prm.M - 1);
+    gx = min(max(gx, 0), prm.N - 1);
+    if constexpr (C::F32IN) {
+        const size_t plane = (size_t)prm.M * prm.N;
+        const float *base = (const float *)prm.img + (size_t)b * 3 * plane + (size_t)gy * prm.N + gx;
+        return make_float4(base[0], base[plane], base[2 * plane], 0.0f);
+    } else {
+        const uint8_t *px = (const uint8_t *)prm.img + 3 * ((size_t)gy * prm.N + gx);
+        const int x = px[0], y = px[1], z = px[2];
+        if constexpr (C::FP64) return make_int4(x, y, z, x * x + y * y + z * z);
+        else return make_float4((float)x, (float)y, (float)z, (float)(x * x + y * y + z * z));
+    }
+}
+
+template <class C>
+__device__ __forceinline__ typename C::PlaneT pair_term(const typename C::Pix &a, const typename C::Pix &b,
+                                                        const Aux &xa, const Aux &xb, int q)
+{
+    typename C::PlaneT t;
+    if constexpr (C::FP64) {
+        double ang, l2 = 0.0;
+        if constexpr (C::F32IN) {
+            ang = aterm64f(a, b);
+            if constexpr (C::FILTER == DDF) l2 = l2term64f(a, b);
+        } else {
+            ang = aterm64<C::DIST>(a, b, q);
+            if constexpr (C::FILTER == DDF) l2 = l2term64(a, b);
+        }
+        if constexpr (C::FILTER == DDF) t = {ang, l2};
+        else t = ang;
+    } else {
+        const PairInts r = pair_ints(a, b);
+        float ang;
+        if constexpr (C::DIST == EXACT) ang = angle32(r);
+        else if constexpr (C::DIST == MINIMAX) ang = minimax32(r, xa, xb, q);
+        else ang = chroma32(a, b, xa, xb);
+        if constexpr (C::FILTER == DDF) t = {ang, l2term32(a, b, r.d)};
+        else t = ang;
+    }
+    return t;
+}
+
+template <class C>
+__device__ __forceinline__ void add_term(typename C::PlaneT &x, const typename C::PlaneT &y)
+{
+    if constexpr (C::FILTER == DDF) {
+        x.a += y.a;
+        x.l += y.l;
+    } else {
+        x += y;
+    }
+}
+
+// Add the horizontal window sums of row offset dy (values g[dx + 2R]) into
+// the aggregates of every window whose rows contain that offset.
+template <class C, int DY>
+__device__ __forceinline__ void accumulate_row(const typename C::PlaneT *g, typename C::PlaneT (*acc)[C::W])
+{
+    constexpr int R = C::R;
+#pragma unroll
+    for (int ex = -R; ex <= R; ++ex) {
+        typename C::PlaneT rs = g[2 * R + (-R - ex)];
+#pragma unroll
+        for (int dx = -R - ex + 1; dx <= R - ex; ++dx) add_term<C>(rs, g[2 * R + dx]);
+#pragma unroll
+        for (int ey = -R; ey <= R; ++ey)
+            if (DY >= -R - ey && DY <= R - ey) add_term<C>(acc[ey + R][ex + R], rs);
+    }
+}
+
+template <class C, int DYP>
+__device__ __forceinline__ void slice(const typename C::Pix *pix, const Aux *aux, typename C::PlaneT *planes,
+                                      int tid, int cy, int cx, const typename C::Pix &self_px, const Aux &self_aux,
+                                      const typename C::PlaneT &self_term, typename C::PlaneT (*acc)[C::W], int q)
+{
+    constexpr int R = C::R, PXW = C::PXW, PLW = C::PLW, PLANE = C::PLH * C::PLW;
+    using PT = typename C::PlaneT;
+    const int pc = (cy + 2 * R) * PLW + (cx + 2 * R);
+    // terms with partners p + (DYP, dx)
+    if (tid < C::NC && cy + DYP < C::CH) {
+        constexpr int K0 = (DYP == 0) ? 1 : -2 * R;
+        constexpr int NK = (DYP == 0) ? 2 * R : 4 * R + 1;
+#pragma unroll
+        for (int k = 0; k < NK; ++k) {
+            const int dx = K0 + k;
+            const int bi = (cy + DYP) * PXW + (cx + 2 * R + dx);
+            Aux xb{};
+            if constexpr (C::AUX) xb = aux[bi];
+            planes[k * PLANE + pc] = pair_term<C>(self_px, pix[bi], self_aux, xb, q);
+        }
+    }
+    __syncthreads();
+    if (tid < C::NC) {
+        PT g[4 * R + 1];
+        if constexpr (DYP == 0) {
+            g[2 * R] = self_term;
+#pragma unroll
+            for (int dx = 1; dx <= 2 * R; ++dx) {
+                g[2 * R + dx] = planes[(dx - 1) * PLANE + pc];
+                g[2 * R - dx] = planes[(dx - 1) * PLANE + pc - dx];
+            }
+            accumulate_row<C, 0>(g, acc);
+        } else {
+#pragma unroll
+            for (int k = 0; k <= 4 * R; ++k) g[k] = planes[k * PLANE + pc];
+            accumulate_row<C, DYP>(g, acc);
+#pragma unroll
+            for (int k = 0; k <= 4 * R; ++k) {
+                const int dx = k - 2 * R;
+                g[k] = planes[(2 * R - dx) * PLANE + pc - DYP * PLW + dx];
+            }
+            accumulate_row<C, -DYP>(g, acc);
+        }
+    }
+    __syncthreads();
+}
+
+template <class C, int... D>
+__device__ __forceinline__ void all_slices(std::integer_sequence<int, D...>, const typename C::Pix *pix,
+                                           const Aux *aux, typename C::PlaneT *planes, int tid, int cy, int cx,
+                                           const typename C::Pix &self_px, const Aux &self_aux,
+                                           const typename C::PlaneT &self_term, typename C::PlaneT (*acc)[C::W],
+                                           int q)
+{
+    (slice<C, D>(pix, aux, planes, tid, cy, cx, self_px, self_aux, self_term, acc, q), ...);
+}
+
+template <class C>
+__global__ void __launch_bounds__(C::NT, 1) tile_kernel(const TileParams prm)
+{
+    constexpr int R = C::R, W = C::W, NW = C::NW, CW = C::CW, PXW = C::PXW;
+    using PT = typename C::PlaneT;
+    using Pix = typename C::Pix;
+    extern __shared__ __align__(16) unsigned char smem[];
+    Pix *pix = reinterpret_cast<Pix *>(smem);
+    Aux *aux = reinterpret_cast<Aux *>(smem + C::PIX_BYTES);
+    PT *planes = reinterpret_cast<PT *>(smem + C::PIX_BYTES + C::AUX_BYTES);
+    typename C::HwT *hw = reinterpret_cast<typename C::HwT *>(smem + C::PIX_BYTES + C::AUX_BYTES);
+
+    const int tid = threadIdx.x;
+    const int b = blockIdx.z;
+    const int y0 = blockIdx.y * C::TH, x0 = blockIdx.x * C::TW;
+
+    // 1. pixels of C plus a 2R column margin on each side, edge-replicated
+    for (int i = tid; i < C::CH * PXW; i += C::NT) {
+        const int r = i / PXW, c = i % PXW;
+        const Pix v = load_pixel<C>(prm, b, y0 - R + r, x0 - 3 * R + c);
+        pix[i] = v;
+        if constexpr (C::AUX) {
+            Aux a;
+            if constexpr (C::DIST == MINIMAX) {
+                a.a = sqrtf(v.w);
+                a.b = v.w > 0.0f ? 1.0f / a.a : 0.0f;
+            } else {
+                a.a = v.x + v.y + v.z;
+                a.b = a.a > 0.0f ? sqrtf(v.w) / a.a : 0.0f;
+            }
+            aux[i] = a;
+        }
+    }
+    __syncthreads();
+
+    // 2. aggregates of the n windows containing this thread's pixel
+    const int cy = tid / CW, cx = tid % CW;
+    const int own = cy * PXW + cx + 2 * R;
+    Pix self_px{};
+    Aux self_aux{};
+    PT self_term{};
+    if (tid < C::NC) {
+        self_px = pix[own];
+        if constexpr (C::AUX) self_aux = aux[own];
+        self_term = pair_term<C>(self_px, self_px, self_aux, self_aux, prm.q);
+    }
+    PT acc[W][W];
+#pragma unroll
+    for (int i = 0; i < W; ++i)
+#pragma unroll
+        for (int j = 0; j < W; ++j) acc[i][j] = PT{};
+    all_slices<C>(std::make_integer_sequence<int, 2 * R + 1>{}, pix, aux, planes, tid, cy, cx, self_px, self_aux,
+                  self_term, acc, prm.q);
+
+    // 3. scores, scattered to the windows of the tile
+    if (tid < C::NC) {
+#pragma unroll
+        for (int ey = -R; ey <= R; ++ey)
+#pragma unroll
+            for (int ex = -R; ex <= R; ++ex) {
+                const int ty = cy - ey - R, tx = cx - ex - R;
+                const int gy = y0 + ty, gx = x0 + tx;
+                if (ty < 0 || ty >= C::TH || tx < 0 || tx >= C::TW || gy >= prm.M || gx >= prm.N) continue;
+                const int e = (ey + R) * W + (ex + R);
+                double sa, sl = 0.0;
+                if constexpr (C::FILTER == DDF) {
+                    sa = acc[ey + R][ex + R].a;
+                    sl = acc[ey + R][ex + R].l;
+                } else {
+                    sa = acc[ey + R][ex + R];
+                }
+                if constexpr (C::FP64) {
+                    if constexpr (C::FILTER == DDF && C::DIST == RGB)
+                        sa = __fma_rn(kSlope64, sa, (double)NW * kOffset64);   // Eq. (10) summed over j
+                    hw[(ty * C::TW + tx) * NW + e] = score64<C::FILTER>(sa, sl, prm.p);
+                    if (prm.agg) {
+                        double *ag = prm.agg + (((size_t)b * prm.M * prm.N + (size_t)gy * prm.N + gx) * NW + e) * 2;
+                        ag[0] = sa;
+                        ag[1] = sl;
+                    }
+                } else {
+                    float saf = (float)sa;
+                    if constexpr (C::FILTER == DDF && C::DIST == RGB)
+                        saf = fmaf(kSlope32, saf, (float)NW * kOffset32);
+                    const float2 fe = score32<R, C::FILTER, C::DIST>(saf, (float)sl, (float)prm.p);
+                    hw[(ty * C::TW + tx) * NW + e] = fe;
+                    if (prm.dbg_fe) {
+                        float *d = prm.dbg_fe + (((size_t)gy * prm.N + gx) * NW + e) * 2;
+                        d[0] = fe.x;
+                        d[1] = fe.y;
+                    }
+                }
+            }
+    }
+    __syncthreads();
+
+    // 4. selection, one thread per output pixel (skipped by the diagnostic
+    //    that only wants the scores)
+    if constexpr (!C::FP64) {
+        if (prm.dbg_fe) return;
+    }
+    if (tid >= C::TW * C::TH) return;
+    const int ty = tid / C::TW, tx = tid % C::TW;
+    const int gy = y0 + ty, gx = x0 + tx;
+    if (gy >= prm.M || gx >= prm.N) return;
+    const auto *f = hw + tid * NW;
+    int sel;
+    if constexpr (C::FP64) {
+        sel = select64<C::FILTER, NW>(f);
+    } else {
+        float U = INFINITY, best = INFINITY;
+        int arg = C::CENTRE;
+#pragma unroll
+        for (int k = 0; k < NW; ++k) {
+            const float2 v = f[k];
+            U = fminf(U, v.x + v.y);
+            if (v.x < best) {
+                best = v.x;
+                arg = k;
+            }
+        }
+        int nnear = 0, first = -1;
+        bool centre_near = false, equal = true, all_zero = true;
+        float4 ref = make_float4(0, 0, 0, 0);
+#pragma unroll
+        for (int k = 0; k < NW; ++k) {
+            const float2 v = f[k];
+            if (v.x - v.y <= U) {
+                const float4 xk = pix[(ty + k / W) * PXW + (tx + k % W) + 2 * R];
+                if (first < 0) {
+                    first = k;
+                    ref = xk;
+                } else {
+                    const bool same = xk.x == ref.x && xk.y == ref.y && xk.z == ref.z;
+                    bool coll = false;
+                    if constexpr (C::FILTER == BVDF) {
+                        // same direction: integer cross product is 0, both non-zero
+                        const float c0 = fmaf(xk.y, ref.z, -(xk.z * ref.y));
+                        const float c1 = fmaf(xk.z, ref.x, -(xk.x * ref.z));
+                        const float c2 = fmaf(xk.x, ref.y, -(xk.y * ref.x));
+                        coll = c0 == 0.0f && c1 == 0.0f && c2 == 0.0f && xk.w > 0.0f && ref.w > 0.0f;
+                    }
+                    equal = equal && (same || coll);
+                }
+                const bool zero = (v.y == 0.0f) &&
+                                  ((C::FILTER == DDF && v.x == -INFINITY) ||
+                                   (C::FILTER == BVDF && C::DIST != MINIMAX && v.x == 0.0f));
+                all_zero = all_zero && zero;
+                centre_near = centre_near || (k == C::CENTRE);
+                ++nnear;
+            }
+        }
+        if (nnear == 1) {
+            sel = first;
+        } else if (equal || all_zero) {
+            sel = centre_near ? C::CENTRE : first;
+        } else {
+            sel = arg;
+            const unsigned slot = atomicAdd(prm.recheck_ctr, 1u);
+            if (slot < prm.recheck_cap) prm.recheck_list[slot] = gy * prm.N + gx;
+            else atomicOr(prm.recheck_ctr + 1, 1u);
+        }
+    }
+    const Pix v = pix[(ty + sel / W) * PXW + (tx + sel % W) + 2 * R];
+    const size_t lin = (size_t)gy * prm.N + gx;
+    if constexpr (C::F32IN) {
+        const size_t plane = (size_t)prm.M * prm.N;
+        float *o = (float *)prm.out + (size_t)b * 3 * plane + lin;
+        o[0] = v.x;
+        o[plane] = v.y;
+        o[2 * plane] = v.z;
+        if (prm.idx) prm.idx[(size_t)b * plane + lin] = (int8_t)sel;
+    } else {
+        uint8_t *o = (uint8_t *)prm.out + 3 * lin;
+        o[0] = (uint8_t)v.x;
+        o[1] = (uint8_t)v.y;
+        o[2] = (uint8_t)v.z;
+        if (prm.idx) prm.idx[lin] = (int8_t)sel;
+    }
+}
+
+template <class C>
+cudaError_t launch_tile(const TileParams &prm, cudaStream_t st)
+{
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(tile_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    dim3 grid((prm.N + C::TW - 1) / C::TW, (prm.M + C::TH - 1) / C::TH, prm.B);
+    tile_kernel<C><<<grid, C::NT, C::SMEM, st>>>(prm);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------- FP64 recheck (one warp
+// per listed pixel): recomputes the window's n scores with the FP64 tile
+// kernel's term function and summation order, so the result equals the FP64
+// path bit for bit.
+
+struct RecheckParams {
+    const uint8_t *img;
+    uint8_t *out;
+    int8_t *idx;
+    const int *list;
+    const unsigned *ctr;
+    unsigned cap;
+    int M, N;
+    double p;
+    int q;
+};
+
+template <int R, int FILTER, int DIST>
+struct RecheckCfg {
+    static constexpr int W = 2 * R + 1, NW = W * W, WARPS = 4;
+    static constexpr int MATS = (FILTER == DDF) ? 2 : 1;
+    // per warp: int4 members first (16-byte aligned), then doubles; the size
+    // is a multiple of 16 so every warp's region stays 16-byte aligned
+    static constexpr size_t PER_WARP = (sizeof(int4) * NW + sizeof(double) * (MATS * NW * NW + NW) + 15) / 16 * 16;
+    static constexpr size_t SMEM = PER_WARP * WARPS;
+};
+
+template <int R, int FILTER, int DIST>
+__global__ void __launch_bounds__(128) recheck_kernel(const RecheckParams prm)
+{
+    using C = RecheckCfg<R, FILTER, DIST>;
+    constexpr int W = C::W, NW = C::NW;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    unsigned char *base = smem + wid * C::PER_WARP;
+    int4 *px = reinterpret_cast<int4 *>(base);
+    double *Ma = reinterpret_cast<double *>(base + sizeof(int4) * NW);
+    double *Ml = Ma + NW * NW;
+    double *fs = Ma + C::MATS * NW * NW;
+
+    const unsigned count = min(prm.ctr[0], prm.cap);
+    const int nwarps = gridDim.x * C::WARPS;
+    for (unsigned it = blockIdx.x * C::WARPS + wid; it < count; it += nwarps) {
+        const int lin = prm.list[it];
+        const int gy = lin / prm.N, gx = lin % prm.N;
+        for (int k = lane; k < NW; k += 32) {
+            const int yy = min(max(gy + k / W - R, 0), prm.M - 1);
+            const int xx = min(max(gx + k % W - R, 0), prm.N - 1);
+            const uint8_t *s = prm.img + 3 * ((size_t)yy * prm.N + xx);
+            const int x = s[0], y = s[1], z = s[2];
+            px[k] = make_int4(x, y, z, x * x + y * y + z * z);
+        }
+        __syncwarp();
+        for (int t = lane; t < NW * NW; t += 32) {
+            const int i = t / NW, j = t % NW;
+            if (i > j) continue;
+            const double a = aterm64<DIST>(px[i], px[j], prm.q);
+            Ma[i * NW + j] = a;
+            Ma[j * NW + i] = a;
+            if constexpr (FILTER == DDF) {
+                const double l = l2term64(px[i], px[j]);
+                Ml[i * NW + j] = l;
+                Ml[j * NW + i] = l;
+            }
+        }
+        __syncwarp();
+        if (lane < NW) {
+            const int ey = lane / W - R, ex = lane % W - R;
+            double sa = 0.0, sl = 0.0;
+            // dy order 0, +1, -1, +2, -2, ... restricted to the window's rows
+            for (int s = 0; s <= 4 * R; ++s) {
+                const int dy = (s == 0) ? 0 : ((s & 1) ? (s + 1) / 2 : -(s / 2));
+                if (dy < -R - ey || dy > R - ey) continue;
+                const int row = (ey + dy + R) * W;
+                const int c0 = ex + (-R - ex) + R;   // column of dx = -R-ex, i.e. 0
+                double ra = Ma[lane * NW + row + c0], rl = 0.0;
+                if constexpr (FILTER == DDF) rl = Ml[lane * NW + row + c0];
+                for (int c = c0 + 1; c < W; ++c) {
+                    ra += Ma[lane * NW + row + c];
+                    if constexpr (FILTER == DDF) rl += Ml[lane * NW + row + c];
+                }
+                sa += ra;
+                sl += rl;
+            }
+            if constexpr (FILTER == DDF && DIST == RGB) sa = __fma_rn(kSlope64, sa, (double)NW * kOffset64);
+            fs[lane] = score64<FILTER>(sa, sl, prm.p);
+        }
+        __syncwarp();
+        if (lane == 0) {
+            const int sel = select64<FILTER, NW>(fs);
+            const int4 v = px[sel];
+            uint8_t *o = prm.out + 3 * (size_t)lin;
+            o[0] = (uint8_t)v.x;
+            o[1] = (uint8_t)v.y;
+            o[2] = (uint8_t)v.z;
+            if (prm.idx) prm.idx[lin] = (int8_t)sel;
+        }
+        __syncwarp();
+    }
+}
+
+template <int R, int FILTER, int DIST>
+cudaError_t launch_recheck(const RecheckParams &prm, int blocks, cudaStream_t st)
+{
+    using C = RecheckCfg<R, FILTER, DIST>;
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(recheck_kernel<R, FILTER, DIST>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    recheck_kernel<R, FILTER, DIST><<<blocks, 32 * C::WARPS, C::SMEM, st>>>(prm);
+    return cudaGetLastError();
+}
+
+}  // namespace vdf

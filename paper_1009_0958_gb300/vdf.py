@@ -1,0 +1,155 @@
+"""ctypes binding of libvdf (C ABI in include/vdf.h).
+
+Argument marshalling only: tensors are passed as raw device pointers with
+their sizes, the stream is torch's current CUDA stream, and every step of the
+filter runs in the library's CUDA kernels.  There is no CPU fallback: if the
+library or a GPU is missing, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+from . import build as _build
+
+FILTERS = {"bvdf": 0, "ddf": 1}
+DISTS = {"exact": 0, "minimax": 1, "rgb": 2}
+PRECISIONS = {"fp64": 0, "fp32": 1}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class VdfError(RuntimeError):
+    pass
+
+
+def lib():
+    """Load libvdf.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(_build.LIB):
+                raise VdfError(f"libvdf.so not built ({_build.LIB}); run paper_1009_0958_gb300.build.build()")
+            L = ctypes.CDLL(_build.LIB)
+            P, i, d, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+            L.vdf_strerror.argtypes, L.vdf_strerror.restype = [i], ctypes.c_char_p
+            L.vdf_last_cuda_error.argtypes, L.vdf_last_cuda_error.restype = [], ctypes.c_char_p
+            L.vdf_workspace_bytes.argtypes, L.vdf_workspace_bytes.restype = [i, i, i], sz
+            L.vdf_host_buffer_bytes.argtypes, L.vdf_host_buffer_bytes.restype = [i, i, i], sz
+            L.vdf_filter.argtypes = [P, i, i, i, i, d, i, i, i, P, P, P, P, sz, P]
+            L.vdf_filter_host.argtypes = [P, i, i, i, i, d, i, i, i, P, P, P, sz, P]
+            L.vdf_fp32_pass.argtypes = [P, i, i, i, i, d, i, i, P, P, P, sz, P]
+            L.vdf_fp64_recheck.argtypes = [P, i, i, i, i, d, i, i, P, P, P, sz, P]
+            L.vdf_workspace_stats.argtypes = [P, P, P, P]
+            L.vdf_debug_fp32_scores.argtypes = [P, i, i, i, i, d, i, i, P, P]
+            for f in ("vdf_filter", "vdf_filter_host", "vdf_workspace_stats", "vdf_debug_fp32_scores",
+                      "vdf_fp32_pass", "vdf_fp64_recheck"):
+                getattr(L, f).restype = i
+            _lib = L
+    return _lib
+
+
+def _check(rc: int):
+    if rc != 0:
+        L = lib()
+        msg = L.vdf_strerror(rc).decode()
+        if rc == -2:
+            msg += ": " + L.vdf_last_cuda_error().decode()
+        raise VdfError(f"libvdf error {rc}: {msg}")
+
+
+def _code(table, v):
+    return table[v] if isinstance(v, str) else int(v)
+
+
+def _stream(stream):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def workspace_bytes(M: int, N: int, precision="fp32") -> int:
+    return int(lib().vdf_workspace_bytes(M, N, _code(PRECISIONS, precision)))
+
+
+def alloc_workspace(M: int, N: int, precision="fp32", device=None) -> torch.Tensor | None:
+    n = workspace_bytes(M, N, precision)
+    if n == 0:
+        return None
+    return torch.empty(n + 256, dtype=torch.uint8, device=device or "cuda")
+
+
+def _aligned(ws: torch.Tensor | None):
+    if ws is None:
+        return None, 0
+    p = ws.data_ptr()
+    off = (-p) % 256
+    return ctypes.c_void_p(p + off), ws.numel() - off
+
+
+def filter(img: torch.Tensor, win: int = 3, filter="bvdf", p: float = 0.5, dist="exact", q: int = 4,
+           precision="fp32", out: torch.Tensor | None = None, index: torch.Tensor | None = None,
+           want_index: bool = True, agg: torch.Tensor | None = None, workspace: torch.Tensor | None = None,
+           stream=None):
+    """Filter an M x N x 3 uint8 CUDA image.  Returns ``(out, index)``."""
+    if not (img.is_cuda and img.dtype == torch.uint8 and img.dim() == 3 and img.shape[2] == 3):
+        raise VdfError("img must be a CUDA uint8 tensor of shape (M, N, 3)")
+    img = img.contiguous()
+    M, N = int(img.shape[0]), int(img.shape[1])
+    if out is None:
+        out = torch.empty_like(img)
+    if index is None and want_index:
+        index = torch.empty((M, N), dtype=torch.int8, device=img.device)
+    prec = _code(PRECISIONS, precision)
+    if workspace is None:
+        workspace = alloc_workspace(M, N, prec, img.device)
+    wp, wn = _aligned(workspace)
+    _check(lib().vdf_filter(_ptr(img), M, N, win, _code(FILTERS, filter), float(p), _code(DISTS, dist), q, prec,
+                            _ptr(out), _ptr(index), _ptr(agg), wp, wn, _stream(stream)))
+    return out, index
+
+
+def workspace_stats(workspace: torch.Tensor, stream=None):
+    """(pixels rechecked in FP64, overflow flag) of the last call using it."""
+    r = ctypes.c_int64(0)
+    o = ctypes.c_int32(0)
+    wp, _ = _aligned(workspace)
+    _check(lib().vdf_workspace_stats(wp, ctypes.byref(r), ctypes.byref(o), _stream(stream)))
+    return int(r.value), int(o.value)
+
+
+def host_buffer_bytes(M: int, N: int, precision="fp32") -> int:
+    return int(lib().vdf_host_buffer_bytes(M, N, _code(PRECISIONS, precision)))
+
+
+def filter_host(img_host: torch.Tensor, win=3, filter="bvdf", p=0.5, dist="exact", q=4, precision="fp32",
+                out_host: torch.Tensor | None = None, index_host: torch.Tensor | None = None,
+                dev_buffer: torch.Tensor | None = None, stream=None):
+    """Filter a host (ideally pinned) uint8 M x N x 3 image end to end: the
+    library copies it in, filters and copies the result back, then waits."""
+    M, N = int(img_host.shape[0]), int(img_host.shape[1])
+    prec = _code(PRECISIONS, precision)
+    if out_host is None:
+        out_host = torch.empty_like(img_host)
+    if dev_buffer is None:
+        dev_buffer = torch.empty(host_buffer_bytes(M, N, prec) + 256, dtype=torch.uint8, device="cuda")
+    bp, bn = _aligned(dev_buffer)
+    _check(lib().vdf_filter_host(_ptr(img_host), M, N, win, _code(FILTERS, filter), float(p), _code(DISTS, dist), q,
+                                 prec, _ptr(out_host), _ptr(index_host), bp, bn, _stream(stream)))
+    return out_host, index_host
+
+
+def debug_fp32_scores(img: torch.Tensor, win=3, filter="bvdf", p=0.5, dist="exact", q=4, stream=None):
+    """Per-member FP32 scores and certified bounds, shape (M, N, n, 2)."""
+    M, N = int(img.shape[0]), int(img.shape[1])
+    fe = torch.full((M, N, win * win, 2), float("nan"), dtype=torch.float32, device=img.device)
+    _check(lib().vdf_debug_fp32_scores(_ptr(img.contiguous()), M, N, win, _code(FILTERS, filter), float(p),
+                                       _code(DISTS, dist), q, _ptr(fe), _stream(stream)))
+    return fe

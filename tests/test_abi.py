@@ -1,0 +1,57 @@
+"""The C ABI library loads and exports every function vdf.h declares; host-side
+argument checks answer without touching a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from tests.conftest import ROOT
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_1009_0958_gb300 import build, vdf
+    build.build()
+    return vdf.lib()
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "vdf.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(vdf_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_exports_every_declared_symbol(L):
+    names = declared_functions()
+    assert len(names) >= 8
+    for n in names:
+        assert hasattr(L, n), n
+
+
+def test_strerror_and_sizes(L):
+    for code in (0, -1, -2, -3, -4, -5, -6):
+        assert L.vdf_strerror(code)
+    assert L.vdf_workspace_bytes(1080, 1920, 0) == 0
+    assert L.vdf_workspace_bytes(1080, 1920, 1) >= 4 * 1080 * 1920
+    assert L.vdf_workspace_bytes(0, 10, 1) == 0
+    assert L.vdf_host_buffer_bytes(10, 10, 1) >= 700
+
+
+@pytest.mark.parametrize("args", [
+    dict(img=None), dict(M=0), dict(N=-1), dict(win=4), dict(win=7), dict(filter=2), dict(filter=1, p=1.5), dict(filter=1, p=-0.1),
+    dict(dist=3), dict(dist=1, q=5), dict(precision=2),
+])
+def test_invalid_arguments_rejected_on_host(L, args):
+    a = dict(img=ctypes.c_void_p(0x10000), M=8, N=8, win=3, filter=0, p=0.5, dist=0, q=4, precision=0,
+             out=ctypes.c_void_p(0x20000))
+    a.update(args)
+    rc = L.vdf_filter(a["img"], a["M"], a["N"], a["win"], a["filter"], a["p"], a["dist"], a["q"], a["precision"],
+                      a["out"], None, None, None, 0, None)
+    assert rc == -1
+
+
+def test_aliasing_and_workspace_checks(L):
+    p = ctypes.c_void_p(0x10000)
+    assert L.vdf_filter(p, 8, 8, 3, 0, 0.5, 0, 4, 0, p, None, None, None, 0, None) == -1      # out == img
+    assert L.vdf_filter(p, 8, 8, 3, 0, 0.5, 0, 4, 1, ctypes.c_void_p(0x20000), None, None, None, 0, None) == -5
