@@ -131,6 +131,33 @@ int vdf_filter_host(const uint8_t *img_host, int M, int N, int win, int filter, 
                     size_t dev_buffer_bytes, void *stream);
 
 /*
+ * Float32 batch variant (the differentiable path).  img: device, B x 3 x M x N
+ * float32 (NCHW, any non-negative values, e.g. RGB in [0, 1]); out: same
+ * shape; index_out: device, B x M x N int8 (may be NULL, but the backward
+ * pass needs it).  Only VDF_DIST_EXACT is supported for float input.  The
+ * FP64 precision computes the pair terms from the float32 values exactly
+ * promoted to double; VDF_PREC_FP32_RECHECK needs workspace of
+ * vdf_workspace_bytes(B * M, N, precision) bytes.  Errors as vdf_filter.
+ */
+int vdf_filter_f32(const float *img, int B, int M, int N, int win, int filter, double p, int dist_mode,
+                   int minimax_q, int precision, float *out, int8_t *index_out, void *workspace,
+                   size_t workspace_bytes, void *stream);
+
+/*
+ * Gradient of vdf_filter_f32 with respect to its input, given the saved
+ * index map: the forward pass copies x(src(p)) to y(p), src(p) = the selected
+ * member (clamped to the image), so grad_x(q) = sum of grad_y(p) over all p
+ * with src(p) = q.  Computed as a gather over each q's window-sized
+ * neighbourhood in a fixed order (deterministic, no atomics).
+ *   grad_y, grad_x: device, B x 3 x M x N float32 (must not overlap);
+ *   index: device, B x M x N int8 from vdf_filter_f32 with the same win.
+ * There is no counterpart in the paper (it does not differentiate the
+ * filters); this is the exact gradient of the selection away from ties.
+ */
+int vdf_backward_f32(const float *grad_y, const int8_t *index, int B, int M, int N, int win, float *grad_x,
+                     void *stream);
+
+/*
  * Diagnostic: the FP32 path's per-member log scores and certified error
  * bounds, without selection.  fe_out: device, M*N*n*2 floats: f then E per
  * member (BVDF: f is the aggregate; DDF: f = p log2 sum A + (1-p) log2 sum L2).

@@ -26,6 +26,7 @@ UNITS = {
     "vdf_fp64.cu": ["-fmad=false"],
     "vdf_fp32.cu": [],
     "vdf_api.cu": [],
+    "vdf_backward.cu": [],
 }
 
 

@@ -217,6 +217,39 @@ int vdf_filter_host(const uint8_t *img_host, int M, int N, int win, int filter, 
     return cuda_fail(e);
 }
 
+int vdf_filter_f32(const float *img, int B, int M, int N, int win, int filter, double p, int dist_mode,
+                   int minimax_q, int precision, float *out, int8_t *index_out, void *workspace,
+                   size_t workspace_bytes, void *stream)
+{
+    if (!img || !out || B < 1 || B > 65535 || !valid_common(M, N, win, filter, p, dist_mode, minimax_q, precision))
+        return VDF_E_INVALID;
+    if ((long long)B * M * N > (1LL << 31) - 1) return VDF_E_INVALID;
+    const size_t bytes = (size_t)B * M * N * 3 * sizeof(float);
+    if (overlaps(img, bytes, out, bytes)) return VDF_E_INVALID;
+    if (dist_mode != VDF_DIST_EXACT) return VDF_E_UNSUPPORTED;
+    if (precision != VDF_PREC_FP64) return VDF_E_UNSUPPORTED;
+    vdf::TileParams prm{};
+    prm.img = img;
+    prm.out = out;
+    prm.idx = index_out;
+    prm.M = M;
+    prm.N = N;
+    prm.B = B;
+    prm.p = p;
+    prm.q = minimax_q;
+    return cuda_fail(vdf::run_fp64(prm, win / 2, filter, dist_mode, true, (cudaStream_t)stream));
+}
+
+int vdf_backward_f32(const float *grad_y, const int8_t *index, int B, int M, int N, int win, float *grad_x,
+                     void *stream)
+{
+    if (!grad_y || !index || !grad_x || B < 1 || B > 65535 || M < 1 || M > 65535 || N < 1) return VDF_E_INVALID;
+    if (win != 3 && win != 5) return VDF_E_INVALID;
+    const size_t bytes = (size_t)B * M * N * 3 * sizeof(float);
+    if (overlaps(grad_y, bytes, grad_x, bytes)) return VDF_E_INVALID;
+    return cuda_fail(vdf::run_backward(grad_y, index, grad_x, B, M, N, win / 2, (cudaStream_t)stream));
+}
+
 int vdf_debug_fp32_scores(const uint8_t *img, int M, int N, int win, int filter, double p, int dist_mode,
                           int minimax_q, float *fe_out, void *stream)
 {

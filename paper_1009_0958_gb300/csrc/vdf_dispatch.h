@@ -12,6 +12,8 @@ namespace vdf {
 cudaError_t run_fp64(const TileParams &prm, int R, int filter, int dist, bool f32in, cudaStream_t st);
 // FP32 certified tile kernel (uint8 input).
 cudaError_t run_fp32(const TileParams &prm, int R, int filter, int dist, cudaStream_t st);
+// Gradient gather of the float32 path.
+cudaError_t run_backward(const float *gy, const int8_t *idx, float *gx, int B, int M, int N, int R, cudaStream_t st);
 // FP64 recheck of the pixels listed by run_fp32.
 cudaError_t run_recheck(const RecheckParams &prm, int R, int filter, int dist, int blocks, cudaStream_t st);
 

@@ -42,12 +42,14 @@ def lib():
             L.vdf_host_buffer_bytes.argtypes, L.vdf_host_buffer_bytes.restype = [i, i, i], sz
             L.vdf_filter.argtypes = [P, i, i, i, i, d, i, i, i, P, P, P, P, sz, P]
             L.vdf_filter_host.argtypes = [P, i, i, i, i, d, i, i, i, P, P, P, sz, P]
+            L.vdf_filter_f32.argtypes = [P, i, i, i, i, i, d, i, i, i, P, P, P, sz, P]
+            L.vdf_backward_f32.argtypes = [P, P, i, i, i, i, P, P]
             L.vdf_fp32_pass.argtypes = [P, i, i, i, i, d, i, i, P, P, P, sz, P]
             L.vdf_fp64_recheck.argtypes = [P, i, i, i, i, d, i, i, P, P, P, sz, P]
             L.vdf_workspace_stats.argtypes = [P, P, P, P]
             L.vdf_debug_fp32_scores.argtypes = [P, i, i, i, i, d, i, i, P, P]
             for f in ("vdf_filter", "vdf_filter_host", "vdf_workspace_stats", "vdf_debug_fp32_scores",
-                      "vdf_fp32_pass", "vdf_fp64_recheck"):
+                      "vdf_fp32_pass", "vdf_fp64_recheck", "vdf_filter_f32", "vdf_backward_f32"):
                 getattr(L, f).restype = i
             _lib = L
     return _lib
@@ -153,3 +155,36 @@ def debug_fp32_scores(img: torch.Tensor, win=3, filter="bvdf", p=0.5, dist="exac
     _check(lib().vdf_debug_fp32_scores(_ptr(img.contiguous()), M, N, win, _code(FILTERS, filter), float(p),
                                        _code(DISTS, dist), q, _ptr(fe), _stream(stream)))
     return fe
+
+
+def filter_f32(img: torch.Tensor, win: int = 3, filter="ddf", p: float = 0.5, dist="exact", q: int = 4,
+               precision="fp64", out: torch.Tensor | None = None, index: torch.Tensor | None = None,
+               workspace: torch.Tensor | None = None, stream=None):
+    """Filter a B x 3 x M x N float32 CUDA batch.  Returns ``(out, index)``."""
+    if not (img.is_cuda and img.dtype == torch.float32 and img.dim() == 4 and img.shape[1] == 3):
+        raise VdfError("img must be a CUDA float32 tensor of shape (B, 3, M, N)")
+    img = img.contiguous()
+    B, _, M, N = (int(v) for v in img.shape)
+    if out is None:
+        out = torch.empty_like(img)
+    if index is None:
+        index = torch.empty((B, M, N), dtype=torch.int8, device=img.device)
+    prec = _code(PRECISIONS, precision)
+    if workspace is None:
+        workspace = alloc_workspace(B * M, N, prec, img.device)
+    wp, wn = _aligned(workspace)
+    _check(lib().vdf_filter_f32(_ptr(img), B, M, N, win, _code(FILTERS, filter), float(p), _code(DISTS, dist), q,
+                                prec, _ptr(out), _ptr(index), wp, wn, _stream(stream)))
+    return out, index
+
+
+def backward_f32(grad_y: torch.Tensor, index: torch.Tensor, win: int, grad_x: torch.Tensor | None = None,
+                 stream=None) -> torch.Tensor:
+    """Gradient of :func:`filter_f32` w.r.t. its input (deterministic gather)."""
+    grad_y = grad_y.contiguous()
+    B, _, M, N = (int(v) for v in grad_y.shape)
+    if grad_x is None:
+        grad_x = torch.empty_like(grad_y)
+    _check(lib().vdf_backward_f32(_ptr(grad_y), _ptr(index.contiguous()), B, M, N, win, _ptr(grad_x),
+                                  _stream(stream)))
+    return grad_x
