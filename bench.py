@@ -165,7 +165,12 @@ def run_reference(args):
     img = frames(1)[0]
     cores = oracle.max_threads()
     rng = np.random.default_rng(1)
-    per_step = 16384
+    # size each step so that warm-up + timed steps take about a minute
+    probe = rng.integers(0, M * N, 2000 * max(1, cores))
+    t0 = time.perf_counter()
+    oracle.filter_u8(img, WIN, FILTER, P, DIST, Q, pixels=probe)
+    rate = len(probe) / (time.perf_counter() - t0)
+    per_step = int(min(65536, max(64, rate * 60.0 / (args.steps + args.warmup))))
     for _ in range(args.warmup):
         oracle.filter_u8(img, WIN, FILTER, P, DIST, Q, pixels=rng.integers(0, M * N, per_step))
     t0 = time.perf_counter()
@@ -186,8 +191,8 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=None)
