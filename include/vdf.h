@@ -158,6 +158,26 @@ int vdf_backward_f32(const float *grad_y, const int8_t *index, int B, int M, int
                      void *stream);
 
 /*
+ * vdf_filter with VDF_PREC_FP32_RECHECK for callers that cannot allocate
+ * device memory (where cudaMalloc is forbidden after start-up, such as
+ * real-time loops that must not block on the allocator, or hosts that own all
+ * device memory and pass in only the image buffers).  It takes no workspace:
+ * the recheck counters and list live in a fixed device array inside the
+ * library (256 bytes + 8 MiB, held on every GPU that loads the library until
+ * the process exits).  The paper has no counterpart; this is an interface
+ * convenience.
+ *   - M * N must not exceed 2,097,152 pixels (2^21, e.g. 1920 x 1080);
+ *     larger images return VDF_E_WORKSPACE and launch nothing.
+ *   - The first call on a device looks up the array's device address (which
+ *     may load the library's device code): make it before any stream capture.
+ *   - All calls share the array: calls that overlap on the GPU race and must
+ *     be serialised by the caller.
+ * Other arguments, results and errors as vdf_filter.
+ */
+int vdf_filter_noalloc(const uint8_t *img, int M, int N, int win, int filter, double p, int dist_mode,
+                       int minimax_q, uint8_t *out, int8_t *index_out, void *stream);
+
+/*
  * Diagnostic: the FP32 path's per-member log scores and certified error
  * bounds, without selection.  fe_out: device, M*N*n*2 floats: f then E per
  * member (BVDF: f is the aggregate; DDF: f = p log2 sum A + (1-p) log2 sum L2).

@@ -27,6 +27,7 @@ UNITS = {
     "vdf_fp32.cu": [],
     "vdf_api.cu": [],
     "vdf_backward.cu": [],
+    "vdf_noalloc.cu": [],
 }
 
 

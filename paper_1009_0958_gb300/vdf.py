@@ -188,3 +188,27 @@ def backward_f32(grad_y: torch.Tensor, index: torch.Tensor, win: int, grad_x: to
     _check(lib().vdf_backward_f32(_ptr(grad_y), _ptr(index.contiguous()), B, M, N, win, _ptr(grad_x),
                                   _stream(stream)))
     return grad_x
+
+
+NOALLOC_MAX_PIXELS = 1 << 21
+
+
+def filter_noalloc(img: torch.Tensor, win: int = 3, filter="bvdf", p: float = 0.5, dist="exact", q: int = 4,
+                   out: torch.Tensor | None = None, index: torch.Tensor | None = None, stream=None):
+    """The FP32 certified filter through ``vdf_filter_noalloc``: no workspace,
+    the library's fixed device scratch (at most 2^21 pixels) is used instead."""
+    L = lib()
+    fn = L.vdf_filter_noalloc
+    if fn.argtypes is None:
+        P, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+        fn.argtypes = [P, i, i, i, i, d, i, i, P, P, P]
+        fn.restype = i
+    img = img.contiguous()
+    M, N = int(img.shape[0]), int(img.shape[1])
+    if out is None:
+        out = torch.empty_like(img)
+    if index is None:
+        index = torch.empty((M, N), dtype=torch.int8, device=img.device)
+    _check(fn(_ptr(img), M, N, win, _code(FILTERS, filter), float(p), _code(DISTS, dist), q, _ptr(out), _ptr(index),
+              _stream(stream)))
+    return out, index
