@@ -188,6 +188,70 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def batch_images(count: int, seed: int):
+    """The uneven-batch workload: sides log-uniform in [64, 2048] (aspect
+    0.5-2), each image cropped from one of four 2048x2048 sinusoid fields,
+    with 3 flat rectangles and 10% impulses of its own."""
+    from paper_1009_0958_gb300 import synth
+    bases = [synth.sinusoid_field(2048, 2048, seed + b) for b in range(4)]
+    rng = np.random.default_rng(seed)
+    out = []
+    for k, (M, N) in enumerate(synth.batch_shapes(count, seed)):
+        M, N = min(M, 2048), min(N, 2048)
+        r0, c0 = int(rng.integers(0, 2048 - M + 1)), int(rng.integers(0, 2048 - N + 1))
+        img = bases[k % 4][r0:r0 + M, c0:c0 + N]
+        img = synth.add_rectangles(img, seed + 10 * k + 1, 3)
+        out.append(synth.impulsive_noise(img, NOISE, seed + 10 * k + 2))
+    return out
+
+
+def run_batch_workload(args):
+    """256 uneven images, mixed 3x3/5x5 BVDF/DDF, one persistent launch per
+    batch replayed from a CUDA graph, tile shapes from the autotuner."""
+    import torch
+
+    from paper_1009_0958_gb300 import build as vbuild
+    from paper_1009_0958_gb300 import vdf
+    vbuild.build()
+    dev = torch.device("cuda", 0)
+    imgs = batch_images(256, 4242)
+    rng = np.random.default_rng(7)
+    cfgs = [(int(rng.choice([3, 5])), str(rng.choice(["bvdf", "ddf"]))) for _ in imgs]
+    probe = torch.from_numpy(frames(1)[0]).to(dev)
+    tuned = {}
+    for win in (3, 5):
+        for f in ("bvdf", "ddf"):
+            tuned[f"{f}{win}x{win}"] = vdf.autotune(probe, win, f, P, reps=5)
+    items = [dict(img=torch.from_numpy(x).to(dev), win=w, filter=f, p=P) for x, (w, f) in zip(imgs, cfgs)]
+    plan = vdf.Plan(items)
+    pixels = sum(int(x.shape[0]) * int(x.shape[1]) for x in imgs)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(args.warmup):
+        plan.graph_launch()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    K = args.steps
+    with ClockSampler(0) as clk:
+        e0.record(stream)
+        for _ in range(K):
+            plan.graph_launch()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / K
+    rechecked, overflow = plan.stats()
+    line = {"metric": "Mpix/s, batch of 256 uneven RGB images, mixed 3x3/5x5 BVDF/DDF, FP32+FP64-tie path",
+            "value": pixels / (ms * 1e-3) / 1e6, "unit": UNIT, "n_gpus": 1, "steps": K, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": "256 images, sides log-uniform [64, 2048], aspect 0.5-2, 10% impulses, "
+                                   "win/filter uniform over {3,5} x {BVDF, DDF}, p = 0.25, exact arccos",
+                       "pixels": pixels, "launch": "one persistent tile kernel + one recheck kernel per step, "
+                                                   "replayed from a CUDA graph", "tuned_shapes": tuned},
+            "recheck_fraction": rechecked / pixels, "overflow": overflow, "gpu_launches": 2 * K,
+            "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -196,10 +260,13 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=None)
+    ap.add_argument("--workload", default="ddf5_1080p", choices=["ddf5_1080p", "batch"])
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch":
+        return run_batch_workload(args)
 
     import torch
     import torch.distributed as dist

@@ -163,7 +163,7 @@ int vdf_backward_f32(const float *grad_y, const int8_t *index, int B, int M, int
  * real-time loops that must not block on the allocator, or hosts that own all
  * device memory and pass in only the image buffers).  It takes no workspace:
  * the recheck counters and list live in a fixed device array inside the
- * library (256 bytes + 8 MiB, held on every GPU that loads the library until
+ * library (256 bytes + 16 MiB, held on every GPU that loads the library until
  * the process exits).  The paper has no counterpart; this is an interface
  * convenience.
  *   - M * N must not exceed 2,097,152 pixels (2^21, e.g. 1920 x 1080);
@@ -176,6 +176,69 @@ int vdf_backward_f32(const float *grad_y, const int8_t *index, int B, int M, int
  */
 int vdf_filter_noalloc(const uint8_t *img, int M, int N, int win, int filter, double p, int dist_mode,
                        int minimax_q, uint8_t *out, int8_t *index_out, void *stream);
+
+/*
+ * Tile-shape autotuner of the FP32 kernel.  The kernel exists in
+ * vdf_num_tile_shapes() output-tile shapes (vdf_tile_shape gives width x
+ * height).  vdf_autotune times every shape on the given image with the given
+ * configuration (`reps` timed launches each after one warm-up, CUDA events
+ * on `stream`; the call waits for the stream), records the fastest for
+ * (win, filter, dist_mode) in a process-wide table used by vdf_filter,
+ * vdf_fp32_pass and vdf_plan_create, and returns it in *best_shape and its
+ * mean time in *best_ms.  Buffers and workspace as for vdf_fp32_pass (the
+ * image is filtered; out / index_out receive valid results).
+ * vdf_get_tuned_shape / vdf_set_tuned_shape read or restore table entries
+ * (for example from a cache file).  The paper has no counterpart.
+ */
+int vdf_num_tile_shapes(void);
+int vdf_tile_shape(int shape, int *tile_w, int *tile_h);
+int vdf_autotune(const uint8_t *img, int M, int N, int win, int filter, double p, int dist_mode, int minimax_q,
+                 uint8_t *out, int8_t *index_out, void *workspace, size_t workspace_bytes, int reps, void *stream,
+                 int *best_shape, float *best_ms);
+int vdf_get_tuned_shape(int win, int filter, int dist_mode);
+int vdf_set_tuned_shape(int win, int filter, int dist_mode, int shape);
+
+/*
+ * Batches of uneven images in one persistent launch (FP32 certified path,
+ * VDF_DIST_EXACT).  Each image has its own size, window (3 or 5), filter and
+ * DDF exponent.  A plan holds, on the host, one descriptor per image with
+ * the tile shape the autotuner table gives its configuration, and the tile
+ * and pixel offsets of the batch.
+ *   vdf_plan_create      validates the descriptors (the plan keeps a copy;
+ *                        device pointers must stay valid while it is used).
+ *   vdf_plan_workspace_bytes  device workspace: counters, descriptors and a
+ *                        recheck list entry per pixel of the batch.
+ *   vdf_plan_upload      copies the descriptors into `workspace` (once per
+ *                        workspace, before vdf_filter_batch or a capture).
+ *   vdf_filter_batch     zeroes the counters, launches one persistent tile
+ *                        kernel (one CTA per SM; CTAs take (image, tile) work
+ *                        items from an atomic counter) and one persistent FP64
+ *                        recheck kernel.  Stream-ordered, no host sync, no
+ *                        allocation: it can be captured in a CUDA graph.
+ *   vdf_plan_graph_launch  captures vdf_filter_batch into a CUDA graph on the
+ *                        first call for a given workspace, then launches the
+ *                        graph on `stream`.
+ *   vdf_plan_destroy     frees the plan and its graph.
+ * Recheck counters are read with vdf_workspace_stats(workspace, ...).
+ */
+typedef struct {
+    const uint8_t *img;  /* device, M*N*3 */
+    uint8_t *out;        /* device, M*N*3, must not overlap img */
+    int8_t *index_out;   /* device, M*N, or NULL */
+    int M, N;
+    int win;             /* 3 or 5 */
+    int filter;          /* vdf_filter_kind */
+    double p;            /* DDF exponent in [0, 1] */
+} vdf_image_desc;
+
+typedef struct vdf_plan vdf_plan;
+
+int vdf_plan_create(vdf_plan **plan, const vdf_image_desc *descs, int count, int dist_mode, int minimax_q);
+size_t vdf_plan_workspace_bytes(const vdf_plan *plan);
+int vdf_plan_upload(vdf_plan *plan, void *workspace, size_t workspace_bytes, void *stream);
+int vdf_filter_batch(vdf_plan *plan, void *workspace, size_t workspace_bytes, void *stream);
+int vdf_plan_graph_launch(vdf_plan *plan, void *workspace, size_t workspace_bytes, void *stream);
+void vdf_plan_destroy(vdf_plan *plan);
 
 /*
  * Diagnostic: the FP32 path's per-member log scores and certified error

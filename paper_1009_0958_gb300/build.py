@@ -22,13 +22,15 @@ LIBDIR = os.path.join(PKG, "lib")
 LIB = os.path.join(LIBDIR, "libvdf.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fno-strict-aliasing"]
-UNITS = {
+# extra flags per translation unit; every csrc/*.cu is compiled
+UNIT_FLAGS = {
     "vdf_fp64.cu": ["-fmad=false"],
-    "vdf_fp32.cu": [],
-    "vdf_api.cu": [],
-    "vdf_backward.cu": [],
-    "vdf_noalloc.cu": [],
 }
+
+
+def units() -> dict[str, list[str]]:
+    return {os.path.basename(f): UNIT_FLAGS.get(os.path.basename(f), [])
+            for f in sorted(glob.glob(os.path.join(CSRC, "*.cu")))}
 
 
 def nvcc() -> str:
@@ -63,10 +65,12 @@ def build(force: bool = False, verbose: bool = False) -> str:
         return LIB
     os.makedirs(BUILD, exist_ok=True)
     os.makedirs(LIBDIR, exist_ok=True)
-    with cf.ThreadPoolExecutor(max_workers=len(UNITS)) as ex:
-        objs = list(ex.map(lambda kv: _compile(kv[0], kv[1], verbose), UNITS.items()))
+    todo = units()
+    with cf.ThreadPoolExecutor(max_workers=min(len(todo), os.cpu_count() or 4)) as ex:
+        objs = list(ex.map(lambda kv: _compile(kv[0], kv[1], verbose), todo.items()))
     tmp = LIB + f".tmp{os.getpid()}"
-    res = subprocess.run([nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart_static", "-lrt", "-ldl", "-lpthread"],
+    res = subprocess.run([nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart_static", "-lrt", "-ldl", "-lpthread",
+                          "-Xlinker", "--no-undefined"],
                          capture_output=True, text=True)
     if res.returncode != 0:
         raise RuntimeError(f"link failed:\n{res.stdout}\n{res.stderr}")

@@ -22,7 +22,8 @@ int cuda_fail(cudaError_t e)
 }
 
 // Workspace of the FP32 path: two counters, padding to 256 bytes, then one
-// int32 pixel id per pixel (the recheck list can never overflow).
+// {pixel id, member mask} int2 entry per pixel (the recheck list can never
+// overflow).
 constexpr size_t kCtrBytes = 256;
 
 bool valid_common(int M, int N, int win, int filter, double p, int dist, int q, int prec)
@@ -56,6 +57,17 @@ int num_sms()
     return sms;
 }
 
+// Tile shape of the FP32 kernel per (window, filter, distance mode): shape 0
+// until vdf_autotune or vdf_set_tuned_shape records another.
+std::mutex g_tune_mutex;
+int g_tuned[2][2][3] = {};
+
+int tuned_shape(int win, int filter, int dist)
+{
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    return g_tuned[win / 2 - 1][filter][dist];
+}
+
 }  // namespace
 
 extern "C" {
@@ -80,7 +92,7 @@ size_t vdf_workspace_bytes(int M, int N, int precision)
 {
     if (M < 1 || N < 1) return 0;
     if (precision != VDF_PREC_FP32_RECHECK) return 0;
-    return kCtrBytes + sizeof(int) * (size_t)M * (size_t)N;
+    return kCtrBytes + sizeof(int2) * (size_t)M * (size_t)N;
 }
 
 static int check_filter_args(const uint8_t *img, int M, int N, int win, int filter, double p, int dist_mode,
@@ -113,14 +125,15 @@ static vdf::TileParams tile_params(const uint8_t *img, int M, int N, double p, i
     prm.q = q;
     if (workspace) {
         prm.recheck_ctr = (unsigned *)workspace;
-        prm.recheck_list = (int *)((char *)workspace + kCtrBytes);
+        prm.recheck_list = (int2 *)((char *)workspace + kCtrBytes);
         prm.recheck_cap = (unsigned)((size_t)M * N);
     }
     return prm;
 }
 
-int vdf_fp32_pass(const uint8_t *img, int M, int N, int win, int filter, double p, int dist_mode, int minimax_q,
-                  uint8_t *out, int8_t *index_out, void *workspace, size_t workspace_bytes, void *stream)
+static int fp32_pass_shape(const uint8_t *img, int M, int N, int win, int filter, double p, int dist_mode,
+                           int minimax_q, uint8_t *out, int8_t *index_out, void *workspace, size_t workspace_bytes,
+                           int shape, void *stream)
 {
     int rc = check_filter_args(img, M, N, win, filter, p, dist_mode, minimax_q, VDF_PREC_FP32_RECHECK, out,
                                index_out, nullptr, workspace, workspace_bytes);
@@ -128,8 +141,16 @@ int vdf_fp32_pass(const uint8_t *img, int M, int N, int win, int filter, double 
     cudaStream_t st = (cudaStream_t)stream;
     const vdf::TileParams prm = tile_params(img, M, N, p, minimax_q, out, index_out, nullptr, workspace);
     cudaError_t e = cudaMemsetAsync(prm.recheck_ctr, 0, 2 * sizeof(unsigned), st);
-    if (e == cudaSuccess) e = vdf::run_fp32(prm, win / 2, filter, dist_mode, st);
+    if (e == cudaSuccess) e = vdf::run_fp32(prm, win / 2, filter, dist_mode, shape, st);
     return cuda_fail(e);
+}
+
+int vdf_fp32_pass(const uint8_t *img, int M, int N, int win, int filter, double p, int dist_mode, int minimax_q,
+                  uint8_t *out, int8_t *index_out, void *workspace, size_t workspace_bytes, void *stream)
+{
+    if (!valid_common(M, N, win, filter, p, dist_mode, minimax_q, VDF_PREC_FP32_RECHECK)) return VDF_E_INVALID;
+    return fp32_pass_shape(img, M, N, win, filter, p, dist_mode, minimax_q, out, index_out, workspace,
+                           workspace_bytes, tuned_shape(win, filter, dist_mode), stream);
 }
 
 int vdf_fp64_recheck(const uint8_t *img, int M, int N, int win, int filter, double p, int dist_mode,
@@ -143,7 +164,7 @@ int vdf_fp64_recheck(const uint8_t *img, int M, int N, int win, int filter, doub
     rp.img = img;
     rp.out = out;
     rp.idx = index_out;
-    rp.list = (const int *)((const char *)workspace + kCtrBytes);
+    rp.list = (const int2 *)((const char *)workspace + kCtrBytes);
     rp.ctr = (const unsigned *)workspace;
     rp.cap = (unsigned)((size_t)M * N);
     rp.M = M;
@@ -250,6 +271,82 @@ int vdf_backward_f32(const float *grad_y, const int8_t *index, int B, int M, int
     return cuda_fail(vdf::run_backward(grad_y, index, grad_x, B, M, N, win / 2, (cudaStream_t)stream));
 }
 
+int vdf_num_tile_shapes(void) { return vdf::kNumShapes32; }
+
+int vdf_tile_shape(int shape, int *tile_w, int *tile_h)
+{
+    if (shape < 0 || shape >= vdf::kNumShapes32) return VDF_E_INVALID;
+    if (tile_w) *tile_w = vdf::kShapes32[shape].tw;
+    if (tile_h) *tile_h = vdf::kShapes32[shape].th;
+    return VDF_OK;
+}
+
+int vdf_get_tuned_shape(int win, int filter, int dist_mode)
+{
+    if ((win != 3 && win != 5) || filter < 0 || filter > 1 || dist_mode < 0 || dist_mode > 2) return VDF_E_INVALID;
+    return tuned_shape(win, filter, dist_mode);
+}
+
+int vdf_set_tuned_shape(int win, int filter, int dist_mode, int shape)
+{
+    if ((win != 3 && win != 5) || filter < 0 || filter > 1 || dist_mode < 0 || dist_mode > 2) return VDF_E_INVALID;
+    if (shape < 0 || shape >= vdf::kNumShapes32) return VDF_E_INVALID;
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    g_tuned[win / 2 - 1][filter][dist_mode] = shape;
+    return VDF_OK;
+}
+
+int vdf_autotune(const uint8_t *img, int M, int N, int win, int filter, double p, int dist_mode, int minimax_q,
+                 uint8_t *out, int8_t *index_out, void *workspace, size_t workspace_bytes, int reps, void *stream,
+                 int *best_shape, float *best_ms)
+{
+    int rc = check_filter_args(img, M, N, win, filter, p, dist_mode, minimax_q, VDF_PREC_FP32_RECHECK, out,
+                               index_out, nullptr, workspace, workspace_bytes);
+    if (rc != VDF_OK) return rc;
+    if (reps < 1) reps = 1;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return cuda_fail(e);
+    }
+    float best = 3.4e38f;
+    int bs = 0;
+    for (int s = 0; s < vdf::kNumShapes32 && rc == VDF_OK; ++s) {
+        rc = fp32_pass_shape(img, M, N, win, filter, p, dist_mode, minimax_q, out, index_out, workspace,
+                             workspace_bytes, s, stream);
+        if (rc != VDF_OK) break;
+        e = cudaEventRecord(e0, st);
+        for (int r = 0; r < reps && rc == VDF_OK && e == cudaSuccess; ++r)
+            rc = fp32_pass_shape(img, M, N, win, filter, p, dist_mode, minimax_q, out, index_out, workspace,
+                                 workspace_bytes, s, stream);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) rc = cuda_fail(e);
+        if (rc == VDF_OK && ms / reps < best) {
+            best = ms / reps;
+            bs = s;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != VDF_OK) return rc;
+    vdf_set_tuned_shape(win, filter, dist_mode, bs);
+    // leave a complete result in out / index_out
+    rc = vdf_fp32_pass(img, M, N, win, filter, p, dist_mode, minimax_q, out, index_out, workspace, workspace_bytes,
+                       stream);
+    if (rc == VDF_OK)
+        rc = vdf_fp64_recheck(img, M, N, win, filter, p, dist_mode, minimax_q, out, index_out, workspace,
+                              workspace_bytes, stream);
+    if (best_shape) *best_shape = bs;
+    if (best_ms) *best_ms = best;
+    return rc;
+}
+
 int vdf_debug_fp32_scores(const uint8_t *img, int M, int N, int win, int filter, double p, int dist_mode,
                           int minimax_q, float *fe_out, void *stream)
 {
@@ -263,7 +360,7 @@ int vdf_debug_fp32_scores(const uint8_t *img, int M, int N, int win, int filter,
     prm.B = 1;
     prm.p = p;
     prm.q = minimax_q;
-    return cuda_fail(vdf::run_fp32(prm, win / 2, filter, dist_mode, (cudaStream_t)stream));
+    return cuda_fail(vdf::run_fp32(prm, win / 2, filter, dist_mode, 0, (cudaStream_t)stream));
 }
 
 }  // extern "C"

@@ -10,8 +10,13 @@ namespace vdf {
 
 // FP64 tile kernel (uint8 input, or float32 NCHW input when f32in).
 cudaError_t run_fp64(const TileParams &prm, int R, int filter, int dist, bool f32in, cudaStream_t st);
-// FP32 certified tile kernel (uint8 input).
-cudaError_t run_fp32(const TileParams &prm, int R, int filter, int dist, cudaStream_t st);
+// FP32 certified tile kernel (uint8 input), in one of kNumShapes32 tile shapes.
+struct TileShape {
+    int tw, th;
+};
+constexpr int kNumShapes32 = 3;
+inline constexpr TileShape kShapes32[kNumShapes32] = {{32, 16}, {32, 8}, {16, 16}};
+cudaError_t run_fp32(const TileParams &prm, int R, int filter, int dist, int shape, cudaStream_t st);
 // Gradient gather of the float32 path.
 cudaError_t run_backward(const float *gy, const int8_t *idx, float *gx, int B, int M, int N, int R, cudaStream_t st);
 // FP64 recheck of the pixels listed by run_fp32.

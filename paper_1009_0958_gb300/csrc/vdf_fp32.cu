@@ -1,34 +1,21 @@
-// vdf_fp32.cu -- FP32 instantiations of the tile kernel (certified scores,
-// FP64 recheck list).
+// vdf_fp32.cu -- dispatch of the FP32 tile kernel over its tile shapes.  The
+// shapes are instantiated in vdf_fp32_s<k>.cu; the autotuner picks one per
+// (window, filter, distance mode).
 #include "vdf_dispatch.h"
 
 namespace vdf {
 
-namespace {
+cudaError_t run_fp32_s0(const TileParams &prm, int R, int filter, int dist, cudaStream_t st);
+cudaError_t run_fp32_s1(const TileParams &prm, int R, int filter, int dist, cudaStream_t st);
+cudaError_t run_fp32_s2(const TileParams &prm, int R, int filter, int dist, cudaStream_t st);
 
-template <int R, int FILTER, int DIST>
-cudaError_t go(const TileParams &prm, cudaStream_t st)
+cudaError_t run_fp32(const TileParams &prm, int R, int filter, int dist, int shape, cudaStream_t st)
 {
-    return launch_tile<TileCfg<R, FILTER, DIST, false, false, 32, 16>>(prm, st);
-}
-
-template <int R, int FILTER>
-cudaError_t by_dist(const TileParams &prm, int dist, cudaStream_t st)
-{
-    switch (dist) {
-    case EXACT: return go<R, FILTER, EXACT>(prm, st);
-    case MINIMAX: return go<R, FILTER, MINIMAX>(prm, st);
-    case RGB: return go<R, FILTER, RGB>(prm, st);
+    switch (shape) {
+    case 0: return run_fp32_s0(prm, R, filter, dist, st);
+    case 1: return run_fp32_s1(prm, R, filter, dist, st);
+    case 2: return run_fp32_s2(prm, R, filter, dist, st);
     }
-    return cudaErrorInvalidValue;
-}
-
-}  // namespace
-
-cudaError_t run_fp32(const TileParams &prm, int R, int filter, int dist, cudaStream_t st)
-{
-    if (R == 1) return filter == DDF ? by_dist<1, DDF>(prm, dist, st) : by_dist<1, BVDF>(prm, dist, st);
-    if (R == 2) return filter == DDF ? by_dist<2, DDF>(prm, dist, st) : by_dist<2, BVDF>(prm, dist, st);
     return cudaErrorInvalidValue;
 }
 

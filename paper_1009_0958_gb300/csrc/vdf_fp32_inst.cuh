@@ -1,0 +1,35 @@
+// vdf_fp32_inst.cuh -- instantiation template of the FP32 tile kernel for one
+// tile shape; each vdf_fp32_s<k>.cu instantiates one shape (parallel build).
+#pragma once
+
+#include "vdf_dispatch.h"
+
+namespace vdf {
+
+template <int TW, int TH>
+cudaError_t run_fp32_shape(const TileParams &prm, int R, int filter, int dist, cudaStream_t st)
+{
+    auto go = [&](auto r, auto f, auto d) {
+        return launch_tile<TileCfg<decltype(r)::value, decltype(f)::value, decltype(d)::value, false, false, TW, TH>>(
+            prm, st);
+    };
+    using I = std::integral_constant<int, 0>;
+    (void)sizeof(I);
+    auto by_dist = [&](auto r, auto f) -> cudaError_t {
+        switch (dist) {
+        case EXACT: return go(r, f, std::integral_constant<int, EXACT>{});
+        case MINIMAX: return go(r, f, std::integral_constant<int, MINIMAX>{});
+        case RGB: return go(r, f, std::integral_constant<int, RGB>{});
+        }
+        return cudaErrorInvalidValue;
+    };
+    auto by_filter = [&](auto r) -> cudaError_t {
+        return filter == DDF ? by_dist(r, std::integral_constant<int, DDF>{})
+                             : by_dist(r, std::integral_constant<int, BVDF>{});
+    };
+    if (R == 1) return by_filter(std::integral_constant<int, 1>{});
+    if (R == 2) return by_filter(std::integral_constant<int, 2>{});
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace vdf

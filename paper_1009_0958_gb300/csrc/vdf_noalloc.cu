@@ -2,8 +2,8 @@
 // caller-provided scratch.
 //
 // vdf_filter's FP32 path needs device scratch beyond its inputs and outputs:
-// two counters and the list of pixels to re-evaluate in FP64 (one int32 per
-// pixel).  Normally the caller allocates it (vdf_workspace_bytes).  Some
+// two counters and the list of pixels to re-evaluate in FP64 (one 8-byte
+// entry per pixel).  Normally the caller allocates it (vdf_workspace_bytes).  Some
 // callers cannot: code that runs where cudaMalloc is forbidden or unsafe
 // after start-up (real-time loops that must not block on the allocator or
 // synchronise the device), plug-ins whose host owns all device memory and
@@ -14,7 +14,7 @@
 // Limits and behaviour:
 //   - capacity kMaxPixels = 2^21 = 2,097,152 pixels (enough for 1920 x 1080);
 //     larger images are rejected with VDF_E_WORKSPACE before any launch;
-//   - the array (256 bytes + 8 MiB) is held on every GPU that loads the
+//   - the array (256 bytes + 16 MiB) is held on every GPU that loads the
 //     library, until the process exits;
 //   - the first call on a device looks up the array's device address
 //     (cudaGetSymbolAddress, which may load this library's device code);
@@ -33,7 +33,7 @@ namespace {
 
 constexpr size_t kMaxPixels = (size_t)1 << 21;
 constexpr size_t kCtrBytes = 256;   // counters, padded like the caller workspace
-constexpr size_t kScratchBytes = kCtrBytes + sizeof(int) * kMaxPixels;
+constexpr size_t kScratchBytes = kCtrBytes + sizeof(int2) * kMaxPixels;   // one {pixel, mask} per pixel
 constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];

@@ -37,9 +37,10 @@ struct TileParams {
     int8_t *idx;           // M*N (per image), may be null
     double *agg;           // FP64: M*N*n*2 aggregates, may be null
     float *dbg_fe;         // FP32: M*N*n*2 (score, bound), may be null (diagnostic)
-    int *recheck_list;     // FP32: pixel ids needing the FP64 path
+    int2 *recheck_list;    // FP32: {pixel id, member mask} needing the FP64 path
     unsigned *recheck_ctr; // [0] = count, [1] = overflow flag
     unsigned recheck_cap;
+    int pix_base;          // added to pixel ids in the recheck list (batches)
     int M, N, B;
     double p;
     int q;
@@ -285,24 +286,121 @@ __device__ __forceinline__ void all_slices(std::integer_sequence<int, D...>, con
     (slice<C, D>(pix, aux, planes, tid, cy, cx, self_px, self_aux, self_term, acc, q), ...);
 }
 
+// Step 4 of the tile: the member selection and the stores of one output pixel.
 template <class C>
-__global__ void __launch_bounds__(C::NT, 1) tile_kernel(const TileParams prm)
+__device__ __forceinline__ void select_and_store(const TileParams &prm, int b, int x0, int y0, int tid,
+                                                 const typename C::Pix *pix, const typename C::HwT *hw)
+{
+    constexpr int R = C::R, W = C::W, NW = C::NW, PXW = C::PXW;
+    using Pix = typename C::Pix;
+    const int ty = tid / C::TW, tx = tid % C::TW;
+    const int gy = y0 + ty, gx = x0 + tx;
+    if (gy >= prm.M || gx >= prm.N) return;
+    const auto *f = hw + tid * NW;
+    int sel;
+    if constexpr (C::FP64) {
+        sel = select64<C::FILTER, NW>(f);
+    } else {
+        float U = INFINITY, best = INFINITY;
+        int arg = C::CENTRE;
+#pragma unroll
+        for (int k = 0; k < NW; ++k) {
+            const float2 v = f[k];
+            U = fminf(U, v.x + v.y);
+            if (v.x < best) {
+                best = v.x;
+                arg = k;
+            }
+        }
+        int nnear = 0, first = -1;
+        bool centre_near = false, equal = true, all_zero = true;
+        float4 ref = make_float4(0, 0, 0, 0);
+#pragma unroll
+        for (int k = 0; k < NW; ++k) {
+            const float2 v = f[k];
+            if (v.x - v.y <= U) {
+                const float4 xk = pix[(ty + k / W) * PXW + (tx + k % W) + 2 * R];
+                if (first < 0) {
+                    first = k;
+                    ref = xk;
+                } else {
+                    const bool same = xk.x == ref.x && xk.y == ref.y && xk.z == ref.z;
+                    bool coll = false;
+                    if constexpr (C::FILTER == BVDF) {
+                        // same direction: integer cross product is 0, both non-zero
+                        const float c0 = fmaf(xk.y, ref.z, -(xk.z * ref.y));
+                        const float c1 = fmaf(xk.z, ref.x, -(xk.x * ref.z));
+                        const float c2 = fmaf(xk.x, ref.y, -(xk.y * ref.x));
+                        coll = c0 == 0.0f && c1 == 0.0f && c2 == 0.0f && xk.w > 0.0f && ref.w > 0.0f;
+                    }
+                    equal = equal && (same || coll);
+                }
+                const bool zero = (v.y == 0.0f) &&
+                                  ((C::FILTER == DDF && v.x == -INFINITY) ||
+                                   (C::FILTER == BVDF && C::DIST != MINIMAX && v.x == 0.0f));
+                all_zero = all_zero && zero;
+                centre_near = centre_near || (k == C::CENTRE);
+                ++nnear;
+            }
+        }
+        if (nnear == 1) {
+            sel = first;
+        } else if (equal || all_zero) {
+            sel = centre_near ? C::CENTRE : first;
+        } else {
+            // Members the FP64 path could still place in its tie set: the near
+            // set widened by a margin of 100x the FP64 tie tolerance (1e-11,
+            // relative for BVDF, natural-log units for DDF).  Every other member
+            // is certified worse than the minimum by more than that margin.
+            const float delta = (C::FILTER == BVDF) ? 1e-9f * fmaxf(fabsf(U), 1e-3f) + 1e-12f : 1e-9f;
+            unsigned mask = 0;
+#pragma unroll
+            for (int k = 0; k < NW; ++k) {
+                const float2 v = f[k];
+                if (v.x - v.y <= U + delta) mask |= 1u << k;
+            }
+            sel = arg;
+            const unsigned slot = atomicAdd(prm.recheck_ctr, 1u);
+            if (slot < prm.recheck_cap) prm.recheck_list[slot] = make_int2(prm.pix_base + gy * prm.N + gx, (int)mask);
+            else atomicOr(prm.recheck_ctr + 1, 1u);
+        }
+    }
+    const Pix v = pix[(ty + sel / W) * PXW + (tx + sel % W) + 2 * R];
+    const size_t lin = (size_t)gy * prm.N + gx;
+    if constexpr (C::F32IN) {
+        const size_t plane = (size_t)prm.M * prm.N;
+        float *o = (float *)prm.out + (size_t)b * 3 * plane + lin;
+        o[0] = v.x;
+        o[plane] = v.y;
+        o[2 * plane] = v.z;
+        if (prm.idx) prm.idx[(size_t)b * plane + lin] = (int8_t)sel;
+    } else {
+        uint8_t *o = (uint8_t *)prm.out + 3 * lin;
+        o[0] = (uint8_t)v.x;
+        o[1] = (uint8_t)v.y;
+        o[2] = (uint8_t)v.z;
+        if (prm.idx) prm.idx[lin] = (int8_t)sel;
+    }
+}
+
+
+// Filters the tile with top-left output pixel (x0, y0) of image b.  Called
+// by all NTL >= C::NT threads of the block (every barrier is reached by all).
+template <class C, int NTL>
+__device__ __forceinline__ void tile_body(const TileParams &prm, int b, int x0, int y0, unsigned char *smem)
 {
     constexpr int R = C::R, W = C::W, NW = C::NW, CW = C::CW, PXW = C::PXW;
     using PT = typename C::PlaneT;
     using Pix = typename C::Pix;
-    extern __shared__ __align__(16) unsigned char smem[];
     Pix *pix = reinterpret_cast<Pix *>(smem);
     Aux *aux = reinterpret_cast<Aux *>(smem + C::PIX_BYTES);
     PT *planes = reinterpret_cast<PT *>(smem + C::PIX_BYTES + C::AUX_BYTES);
     typename C::HwT *hw = reinterpret_cast<typename C::HwT *>(smem + C::PIX_BYTES + C::AUX_BYTES);
 
     const int tid = threadIdx.x;
-    const int b = blockIdx.z;
-    const int y0 = blockIdx.y * C::TH, x0 = blockIdx.x * C::TW;
 
     // 1. pixels of C plus a 2R column margin on each side, edge-replicated
-    for (int i = tid; i < C::CH * PXW; i += C::NT) {
+    for (int i = tid; i < C::CH * PXW; i += NTL) {
         const int r = i / PXW, c = i % PXW;
         const Pix v = load_pixel<C>(prm, b, y0 - R + r, x0 - 3 * R + c);
         pix[i] = v;
@@ -383,87 +481,17 @@ __global__ void __launch_bounds__(C::NT, 1) tile_kernel(const TileParams prm)
 
     // 4. selection, one thread per output pixel (skipped by the diagnostic
     //    that only wants the scores)
-    if constexpr (!C::FP64) {
-        if (prm.dbg_fe) return;
-    }
-    if (tid >= C::TW * C::TH) return;
-    const int ty = tid / C::TW, tx = tid % C::TW;
-    const int gy = y0 + ty, gx = x0 + tx;
-    if (gy >= prm.M || gx >= prm.N) return;
-    const auto *f = hw + tid * NW;
-    int sel;
-    if constexpr (C::FP64) {
-        sel = select64<C::FILTER, NW>(f);
-    } else {
-        float U = INFINITY, best = INFINITY;
-        int arg = C::CENTRE;
-#pragma unroll
-        for (int k = 0; k < NW; ++k) {
-            const float2 v = f[k];
-            U = fminf(U, v.x + v.y);
-            if (v.x < best) {
-                best = v.x;
-                arg = k;
-            }
-        }
-        int nnear = 0, first = -1;
-        bool centre_near = false, equal = true, all_zero = true;
-        float4 ref = make_float4(0, 0, 0, 0);
-#pragma unroll
-        for (int k = 0; k < NW; ++k) {
-            const float2 v = f[k];
-            if (v.x - v.y <= U) {
-                const float4 xk = pix[(ty + k / W) * PXW + (tx + k % W) + 2 * R];
-                if (first < 0) {
-                    first = k;
-                    ref = xk;
-                } else {
-                    const bool same = xk.x == ref.x && xk.y == ref.y && xk.z == ref.z;
-                    bool coll = false;
-                    if constexpr (C::FILTER == BVDF) {
-                        // same direction: integer cross product is 0, both non-zero
-                        const float c0 = fmaf(xk.y, ref.z, -(xk.z * ref.y));
-                        const float c1 = fmaf(xk.z, ref.x, -(xk.x * ref.z));
-                        const float c2 = fmaf(xk.x, ref.y, -(xk.y * ref.x));
-                        coll = c0 == 0.0f && c1 == 0.0f && c2 == 0.0f && xk.w > 0.0f && ref.w > 0.0f;
-                    }
-                    equal = equal && (same || coll);
-                }
-                const bool zero = (v.y == 0.0f) &&
-                                  ((C::FILTER == DDF && v.x == -INFINITY) ||
-                                   (C::FILTER == BVDF && C::DIST != MINIMAX && v.x == 0.0f));
-                all_zero = all_zero && zero;
-                centre_near = centre_near || (k == C::CENTRE);
-                ++nnear;
-            }
-        }
-        if (nnear == 1) {
-            sel = first;
-        } else if (equal || all_zero) {
-            sel = centre_near ? C::CENTRE : first;
-        } else {
-            sel = arg;
-            const unsigned slot = atomicAdd(prm.recheck_ctr, 1u);
-            if (slot < prm.recheck_cap) prm.recheck_list[slot] = gy * prm.N + gx;
-            else atomicOr(prm.recheck_ctr + 1, 1u);
-        }
-    }
-    const Pix v = pix[(ty + sel / W) * PXW + (tx + sel % W) + 2 * R];
-    const size_t lin = (size_t)gy * prm.N + gx;
-    if constexpr (C::F32IN) {
-        const size_t plane = (size_t)prm.M * prm.N;
-        float *o = (float *)prm.out + (size_t)b * 3 * plane + lin;
-        o[0] = v.x;
-        o[plane] = v.y;
-        o[2 * plane] = v.z;
-        if (prm.idx) prm.idx[(size_t)b * plane + lin] = (int8_t)sel;
-    } else {
-        uint8_t *o = (uint8_t *)prm.out + 3 * lin;
-        o[0] = (uint8_t)v.x;
-        o[1] = (uint8_t)v.y;
-        o[2] = (uint8_t)v.z;
-        if (prm.idx) prm.idx[lin] = (int8_t)sel;
-    }
+    bool selects = tid < C::TW * C::TH;
+    if constexpr (!C::FP64) selects = selects && !prm.dbg_fe;
+    if (selects) select_and_store<C>(prm, b, x0, y0, tid, pix, hw);
+}
+
+
+template <class C>
+__global__ void __launch_bounds__(C::NT, 1) tile_kernel(const TileParams prm)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    tile_body<C, C::NT>(prm, blockIdx.z, blockIdx.x * C::TW, blockIdx.y * C::TH, smem);
 }
 
 template <class C>
@@ -481,15 +509,17 @@ cudaError_t launch_tile(const TileParams &prm, cudaStream_t st)
 }
 
 // ------------------------------------------------- FP64 recheck (one warp
-// per listed pixel): recomputes the window's n scores with the FP64 tile
-// kernel's term function and summation order, so the result equals the FP64
-// path bit for bit.
+// per listed pixel): recomputes, for the members in the pixel's mask, the
+// window scores with the FP64 tile kernel's term function and summation
+// order, so the result equals the FP64 path bit for bit.  Members outside the
+// mask are certified (by the FP32 bounds) to exceed the minimum by more than
+// the FP64 tie tolerance; they cannot be selected or tie, and are given +inf.
 
 struct RecheckParams {
     const uint8_t *img;
     uint8_t *out;
     int8_t *idx;
-    const int *list;
+    const int2 *list;
     const unsigned *ctr;
     unsigned cap;
     int M, N;
@@ -507,57 +537,52 @@ struct RecheckCfg {
     static constexpr size_t SMEM = PER_WARP * WARPS;
 };
 
+// Recheck of one listed pixel by one warp.  `base` is the warp's shared
+// memory (RecheckCfg::PER_WARP bytes, 16-byte aligned).
 template <int R, int FILTER, int DIST>
-__global__ void __launch_bounds__(128) recheck_kernel(const RecheckParams prm)
+__device__ __forceinline__ void recheck_pixel(const uint8_t *img, int M, int N, int lin, unsigned mask, uint8_t *out,
+                                              int8_t *idx, double p, int q, unsigned char *base, int lane)
 {
     using C = RecheckCfg<R, FILTER, DIST>;
     constexpr int W = C::W, NW = C::NW;
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    unsigned char *base = smem + wid * C::PER_WARP;
     int4 *px = reinterpret_cast<int4 *>(base);
     double *Ma = reinterpret_cast<double *>(base + sizeof(int4) * NW);
     double *Ml = Ma + NW * NW;
     double *fs = Ma + C::MATS * NW * NW;
-
-    const unsigned count = min(prm.ctr[0], prm.cap);
-    const int nwarps = gridDim.x * C::WARPS;
-    for (unsigned it = blockIdx.x * C::WARPS + wid; it < count; it += nwarps) {
-        const int lin = prm.list[it];
-        const int gy = lin / prm.N, gx = lin % prm.N;
-        for (int k = lane; k < NW; k += 32) {
-            const int yy = min(max(gy + k / W - R, 0), prm.M - 1);
-            const int xx = min(max(gx + k % W - R, 0), prm.N - 1);
-            const uint8_t *s = prm.img + 3 * ((size_t)yy * prm.N + xx);
-            const int x = s[0], y = s[1], z = s[2];
-            px[k] = make_int4(x, y, z, x * x + y * y + z * z);
-        }
-        __syncwarp();
-        for (int t = lane; t < NW * NW; t += 32) {
-            const int i = t / NW, j = t % NW;
-            if (i > j) continue;
-            const double a = aterm64<DIST>(px[i], px[j], prm.q);
-            Ma[i * NW + j] = a;
-            Ma[j * NW + i] = a;
-            if constexpr (FILTER == DDF) {
-                const double l = l2term64(px[i], px[j]);
-                Ml[i * NW + j] = l;
-                Ml[j * NW + i] = l;
-            }
-        }
-        __syncwarp();
-        if (lane < NW) {
+    const int gy = lin / N, gx = lin % N;
+    for (int k = lane; k < NW; k += 32) {
+        const int yy = min(max(gy + k / W - R, 0), M - 1);
+        const int xx = min(max(gx + k % W - R, 0), N - 1);
+        const uint8_t *s = img + 3 * ((size_t)yy * N + xx);
+        const int x = s[0], y = s[1], z = s[2];
+        px[k] = make_int4(x, y, z, x * x + y * y + z * z);
+    }
+    __syncwarp();
+    // rows of the masked members: terms (i, j) for i in mask, all j
+    const int cnt = __popc(mask);
+    for (int t = lane; t < cnt * NW; t += 32) {
+        const int r = t / NW, j = t % NW;
+        unsigned mm = mask;
+        for (int s = 0; s < r; ++s) mm &= mm - 1;   // drop the r lowest members
+        const int i = __ffs(mm) - 1;
+        Ma[i * NW + j] = aterm64<DIST>(px[i], px[j], q);
+        if constexpr (FILTER == DDF) Ml[i * NW + j] = l2term64(px[i], px[j]);
+    }
+    __syncwarp();
+    if (lane < NW) {
+        double f = INFINITY;
+        if ((mask >> lane) & 1u) {
             const int ey = lane / W - R, ex = lane % W - R;
             double sa = 0.0, sl = 0.0;
             // dy order 0, +1, -1, +2, -2, ... restricted to the window's rows
             for (int s = 0; s <= 4 * R; ++s) {
                 const int dy = (s == 0) ? 0 : ((s & 1) ? (s + 1) / 2 : -(s / 2));
                 if (dy < -R - ey || dy > R - ey) continue;
+                // the row sum covers the window's full row (dx = -R-ex .. R-ex)
                 const int row = (ey + dy + R) * W;
-                const int c0 = ex + (-R - ex) + R;   // column of dx = -R-ex, i.e. 0
-                double ra = Ma[lane * NW + row + c0], rl = 0.0;
-                if constexpr (FILTER == DDF) rl = Ml[lane * NW + row + c0];
-                for (int c = c0 + 1; c < W; ++c) {
+                double ra = Ma[lane * NW + row], rl = 0.0;
+                if constexpr (FILTER == DDF) rl = Ml[lane * NW + row];
+                for (int c = 1; c < W; ++c) {
                     ra += Ma[lane * NW + row + c];
                     if constexpr (FILTER == DDF) rl += Ml[lane * NW + row + c];
                 }
@@ -565,19 +590,36 @@ __global__ void __launch_bounds__(128) recheck_kernel(const RecheckParams prm)
                 sl += rl;
             }
             if constexpr (FILTER == DDF && DIST == RGB) sa = __fma_rn(kSlope64, sa, (double)NW * kOffset64);
-            fs[lane] = score64<FILTER>(sa, sl, prm.p);
+            f = score64<FILTER>(sa, sl, p);
         }
-        __syncwarp();
-        if (lane == 0) {
-            const int sel = select64<FILTER, NW>(fs);
-            const int4 v = px[sel];
-            uint8_t *o = prm.out + 3 * (size_t)lin;
-            o[0] = (uint8_t)v.x;
-            o[1] = (uint8_t)v.y;
-            o[2] = (uint8_t)v.z;
-            if (prm.idx) prm.idx[lin] = (int8_t)sel;
-        }
-        __syncwarp();
+        fs[lane] = f;
+    }
+    __syncwarp();
+    if (lane == 0) {
+        const int sel = select64<FILTER, NW>(fs);
+        const int4 v = px[sel];
+        uint8_t *o = out + 3 * (size_t)lin;
+        o[0] = (uint8_t)v.x;
+        o[1] = (uint8_t)v.y;
+        o[2] = (uint8_t)v.z;
+        if (idx) idx[lin] = (int8_t)sel;
+    }
+    __syncwarp();
+}
+
+template <int R, int FILTER, int DIST>
+__global__ void __launch_bounds__(128) recheck_kernel(const RecheckParams prm)
+{
+    using C = RecheckCfg<R, FILTER, DIST>;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    unsigned char *base = smem + wid * C::PER_WARP;
+    const unsigned count = min(prm.ctr[0], prm.cap);
+    const int nwarps = gridDim.x * C::WARPS;
+    for (unsigned it = blockIdx.x * C::WARPS + wid; it < count; it += nwarps) {
+        const int2 ent = prm.list[it];
+        recheck_pixel<R, FILTER, DIST>(prm.img, prm.M, prm.N, ent.x, (unsigned)ent.y, prm.out, prm.idx, prm.p, prm.q,
+                                       base, lane);
     }
 }
 

@@ -212,3 +212,128 @@ def filter_noalloc(img: torch.Tensor, win: int = 3, filter="bvdf", p: float = 0.
     _check(fn(_ptr(img), M, N, win, _code(FILTERS, filter), float(p), _code(DISTS, dist), q, _ptr(out), _ptr(index),
               _stream(stream)))
     return out, index
+
+
+# ---------------------------------------------------------------- autotune
+
+def _tune_fns(L):
+    P, i, d, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+    if L.vdf_autotune.argtypes is None:
+        L.vdf_autotune.argtypes = [P, i, i, i, i, d, i, i, P, P, P, sz, i, P, P, P]
+        L.vdf_tile_shape.argtypes = [i, P, P]
+        L.vdf_get_tuned_shape.argtypes = [i, i, i]
+        L.vdf_set_tuned_shape.argtypes = [i, i, i, i]
+        for f in ("vdf_autotune", "vdf_tile_shape", "vdf_get_tuned_shape", "vdf_set_tuned_shape",
+                  "vdf_num_tile_shapes"):
+            getattr(L, f).restype = i
+    return L
+
+
+def tile_shapes():
+    """[(tile_w, tile_h)] of the FP32 kernel's shapes, by shape id."""
+    L = _tune_fns(lib())
+    out = []
+    for s in range(L.vdf_num_tile_shapes()):
+        w, h = ctypes.c_int(), ctypes.c_int()
+        _check(L.vdf_tile_shape(s, ctypes.byref(w), ctypes.byref(h)))
+        out.append((w.value, h.value))
+    return out
+
+
+def autotune(img: torch.Tensor, win=5, filter="ddf", p=0.25, dist="exact", q=4, reps=5, stream=None):
+    """Time every tile shape on `img`; the fastest is recorded for (win,
+    filter, dist) and used by later calls.  Returns (shape_id, ms)."""
+    L = _tune_fns(lib())
+    img = img.contiguous()
+    M, N = int(img.shape[0]), int(img.shape[1])
+    out = torch.empty_like(img)
+    idx = torch.empty((M, N), dtype=torch.int8, device=img.device)
+    ws = alloc_workspace(M, N, "fp32", img.device)
+    wp, wn = _aligned(ws)
+    s, ms = ctypes.c_int(), ctypes.c_float()
+    _check(L.vdf_autotune(_ptr(img), M, N, win, _code(FILTERS, filter), float(p), _code(DISTS, dist), q, _ptr(out),
+                          _ptr(idx), wp, wn, reps, _stream(stream), ctypes.byref(s), ctypes.byref(ms)))
+    return s.value, ms.value
+
+
+def tuned_shape(win, filter="ddf", dist="exact") -> int:
+    return int(_tune_fns(lib()).vdf_get_tuned_shape(win, _code(FILTERS, filter), _code(DISTS, dist)))
+
+
+def set_tuned_shape(win, filter, dist, shape: int):
+    _check(_tune_fns(lib()).vdf_set_tuned_shape(win, _code(FILTERS, filter), _code(DISTS, dist), shape))
+
+
+# ------------------------------------------------------------------- batch
+
+class ImageDesc(ctypes.Structure):
+    _fields_ = [("img", ctypes.c_void_p), ("out", ctypes.c_void_p), ("index_out", ctypes.c_void_p),
+                ("M", ctypes.c_int), ("N", ctypes.c_int), ("win", ctypes.c_int), ("filter", ctypes.c_int),
+                ("p", ctypes.c_double)]
+
+
+class Plan:
+    """A batch of uneven uint8 images filtered in one persistent launch.
+
+    ``items``: list of dicts with keys ``img`` (CUDA uint8 M x N x 3), and
+    optionally ``win`` (3), ``filter`` ("bvdf"), ``p`` (0.5), ``out`` and
+    ``index``.  Outputs are allocated when absent.  The workspace is
+    allocated here (torch), uploaded once, and reused by every launch.
+    """
+
+    def __init__(self, items, dist="exact", q=4, device=None):
+        L = lib()
+        if L.vdf_plan_create.argtypes is None:
+            P, i, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t
+            L.vdf_plan_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), P, i, i, i]
+            L.vdf_plan_workspace_bytes.argtypes, L.vdf_plan_workspace_bytes.restype = [P], sz
+            for f in ("vdf_plan_upload", "vdf_filter_batch", "vdf_plan_graph_launch"):
+                getattr(L, f).argtypes = [P, P, sz, P]
+                getattr(L, f).restype = i
+            L.vdf_plan_create.restype = i
+            L.vdf_plan_destroy.argtypes, L.vdf_plan_destroy.restype = [P], None
+        self._L = L
+        self.items = []
+        descs = (ImageDesc * len(items))()
+        for k, it in enumerate(items):
+            img = it["img"].contiguous()
+            M, N = int(img.shape[0]), int(img.shape[1])
+            out = it.get("out")
+            if out is None:
+                out = torch.empty_like(img)
+            idx = it.get("index")
+            if idx is None:
+                idx = torch.empty((M, N), dtype=torch.int8, device=img.device)
+            rec = dict(img=img, out=out, index=idx, win=int(it.get("win", 3)), filter=it.get("filter", "bvdf"),
+                       p=float(it.get("p", 0.5)))
+            self.items.append(rec)
+            descs[k] = ImageDesc(img.data_ptr(), out.data_ptr(), idx.data_ptr(), M, N, rec["win"],
+                                 _code(FILTERS, rec["filter"]), rec["p"])
+        self._handle = ctypes.c_void_p()
+        _check(L.vdf_plan_create(ctypes.byref(self._handle), ctypes.cast(descs, ctypes.c_void_p), len(items),
+                                 _code(DISTS, dist), q))
+        nbytes = int(L.vdf_plan_workspace_bytes(self._handle))
+        dev = device or self.items[0]["img"].device
+        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=dev)
+        self._wp, self._wn = _aligned(self.workspace)
+        _check(L.vdf_plan_upload(self._handle, self._wp, self._wn, _stream(None)))
+
+    def run(self, stream=None):
+        _check(self._L.vdf_filter_batch(self._handle, self._wp, self._wn, _stream(stream)))
+
+    def graph_launch(self, stream=None):
+        _check(self._L.vdf_plan_graph_launch(self._handle, self._wp, self._wn, _stream(stream)))
+
+    def stats(self, stream=None):
+        return workspace_stats(self.workspace, stream)
+
+    def close(self):
+        if getattr(self, "_handle", None) and self._handle.value:
+            self._L.vdf_plan_destroy(self._handle)
+            self._handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
