@@ -243,8 +243,9 @@ void vdf_plan_destroy(vdf_plan *plan);
 /*
  * Diagnostic: the FP32 path's per-member log scores and certified error
  * bounds, without selection.  fe_out: device, M*N*n*2 floats: f then E per
- * member (BVDF: f is the aggregate; DDF: f = p log2 sum A + (1-p) log2 sum L2).
- * The true score lies in [f - E, f + E].
+ * member.  BVDF: f is the aggregate.  DDF: f = (sum A)^(4p) (sum L2)^(4-4p)
+ * (= Omega^4) when 4p is an integer, else f = p log2 sum A + (1-p) log2
+ * sum L2.  The true value of f lies in [f - E, f + E].
  */
 int vdf_debug_fp32_scores(const uint8_t *img, int M, int N, int win, int filter, double p, int dist_mode,
                           int minimax_q, float *fe_out, void *stream);

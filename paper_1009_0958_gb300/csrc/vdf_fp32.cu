@@ -8,6 +8,7 @@ namespace vdf {
 cudaError_t run_fp32_s0(const TileParams &prm, int R, int filter, int dist, cudaStream_t st);
 cudaError_t run_fp32_s1(const TileParams &prm, int R, int filter, int dist, cudaStream_t st);
 cudaError_t run_fp32_s2(const TileParams &prm, int R, int filter, int dist, cudaStream_t st);
+cudaError_t run_fp32_s3(const TileParams &prm, int R, int filter, int dist, cudaStream_t st);
 
 cudaError_t run_fp32(const TileParams &prm, int R, int filter, int dist, int shape, cudaStream_t st)
 {
@@ -15,6 +16,7 @@ cudaError_t run_fp32(const TileParams &prm, int R, int filter, int dist, int sha
     case 0: return run_fp32_s0(prm, R, filter, dist, st);
     case 1: return run_fp32_s1(prm, R, filter, dist, st);
     case 2: return run_fp32_s2(prm, R, filter, dist, st);
+    case 3: return run_fp32_s3(prm, R, filter, dist, st);
     }
     return cudaErrorInvalidValue;
 }

@@ -14,6 +14,8 @@
 // barrier, p reads its own row (offset +dy') and the mirrored row (offset
 // -dy', written by the pixels above it), forms the horizontal window sums and
 // adds them into the n accumulators of the windows whose rows they belong to.
+// Two plane buffers pipeline the slices: the terms of slice k+1 are computed
+// in the same phase as the accumulation of slice k (2R+2 barriers, not 4R+2).
 //
 // After the slices every thread turns its n aggregates into scores and
 // scatters them to the windows (shared memory), and one thread per output
@@ -60,16 +62,18 @@ struct TileCfg {
     static constexpr bool AUX = !FP64 && (DIST != EXACT);
     using Real = typename std::conditional<FP64, double, float>::type;
     using Pix = typename std::conditional<FP64 && !F32IN, int4, float4>::type;
-    struct Term {
-        Real a, l;
-    };
-    using PlaneT = typename std::conditional<FILTER == DDF, Term, Real>::type;
-    using HwT = typename std::conditional<FP64, double, float2>::type;
+    // DDF terms and aggregates are (angular, L2) pairs: .x and .y
+    using Pair = typename std::conditional<FP64, double2, float2>::type;
+    using PlaneT = typename std::conditional<FILTER == DDF, Pair, Real>::type;
+    // per (window, member) slot: the raw aggregates, later the score in place
+    using HwT = typename std::conditional<FP64, typename std::conditional<FILTER == DDF, double2, double>::type,
+                                          float2>::type;
     static constexpr size_t PIX_BYTES = sizeof(Pix) * CH * PXW;
     static constexpr size_t AUX_BYTES = AUX ? (sizeof(Aux) * CH * PXW + 15) / 16 * 16 : 0;
     static constexpr size_t PLANE_BYTES = sizeof(PlaneT) * NPL * PLH * PLW;
     static constexpr size_t HW_BYTES = sizeof(HwT) * TW * TH * NW;
-    static constexpr size_t UNION_BYTES = PLANE_BYTES > HW_BYTES ? PLANE_BYTES : HW_BYTES;
+    // two plane buffers (slice pipeline), later reused for the per-window scores
+    static constexpr size_t UNION_BYTES = 2 * PLANE_BYTES > HW_BYTES ? 2 * PLANE_BYTES : HW_BYTES;
     static constexpr size_t SMEM = PIX_BYTES + AUX_BYTES + UNION_BYTES;
 };
 
@@ -90,18 +94,18 @@ __device__ __forceinline__ double score64(double sa, double sl, double p)
 // Member selection of the FP64 path: scores within 1e-11 of the minimum
 // (relative with floor 1e-3 for BVDF; absolute in the log domain for DDF)
 // are tied; the centre wins a tie, else the lowest index.
-template <int FILTER, int NW>
-__device__ __forceinline__ int select64(const double *f)
+template <int FILTER, int NW, class F>
+__device__ __forceinline__ int select64(F f)
 {
-    double m = f[0];
-#pragma unroll
-    for (int k = 1; k < NW; ++k) m = fmin(m, f[k]);
+    double m = f(0);
+#pragma unroll 1
+    for (int k = 1; k < NW; ++k) m = fmin(m, f(k));
     const double tol = (FILTER == BVDF) ? 1e-11 * fmax(fabs(m), 1e-3) : 1e-11;
     constexpr int c = (NW - 1) / 2;
-    if (f[c] == m || f[c] - m <= tol) return c;
-#pragma unroll
+    if (f(c) == m || f(c) - m <= tol) return c;
+#pragma unroll 1
     for (int k = 0; k < NW; ++k)
-        if (f[k] == m || f[k] - m <= tol) return k;
+        if (f(k) == m || f(k) - m <= tol) return k;
     return c;   // not reached
 }
 
@@ -110,7 +114,7 @@ __device__ __forceinline__ int select64(const double *f)
 // stages), chromaticity 11 + 4R (+2 for Eq. (10)), L2 6 + 4R; Method 1 has
 // an absolute bound 24u per term plus 4R u |SA|.  Bounds are doubled.
 template <int R, int FILTER, int DIST>
-__device__ __forceinline__ float2 score32(float sa, float sl, float p)
+__device__ __forceinline__ float2 score32(float sa, float sl, float p, int quarter)
 {
     constexpr int NW = (2 * R + 1) * (2 * R + 1);
     constexpr float S = 4.0f * R;
@@ -134,6 +138,16 @@ __device__ __forceinline__ float2 score32(float sa, float sl, float p)
     }
     if (unsure) return make_float2(-1e30f, INFINITY);   // Method 1 sum too close to 0 to take its log
     const float relL = (6.0f + S) * kU;
+    if (quarter >= 0) {
+        // p = a/4: Omega^4 = SA^a SL^(4-a) orders like Omega, with a relative
+        // bound (a relA + (4-a) relL + 3 roundings) and no logarithm
+        const float sa0 = fmaxf(sa, 0.0f);
+        float g = 1.0f;
+        for (int i = 0; i < quarter; ++i) g *= sa0;
+        for (int i = quarter; i < 4; ++i) g *= sl;
+        if (g == 0.0f) return make_float2(0.0f, 0.0f);   // an aggregate is exactly 0
+        return make_float2(g, kSafety * g * (quarter * relA + (4 - quarter) * relL + 3.0f * kU));
+    }
     constexpr float kLg2Abs = 1.6e-7f;   // __log2f on [1,2): 2^-22.6
     constexpr float kInvLn2 = 1.4426950f;
     float f = 0.0f, E = 0.0f, lsum = 0.0f;
@@ -187,7 +201,7 @@ __device__ __forceinline__ typename C::PlaneT pair_term(const typename C::Pix &a
             ang = aterm64<C::DIST>(a, b, q);
             if constexpr (C::FILTER == DDF) l2 = l2term64(a, b);
         }
-        if constexpr (C::FILTER == DDF) t = {ang, l2};
+        if constexpr (C::FILTER == DDF) t = make_double2(ang, l2);
         else t = ang;
     } else {
         const PairInts r = pair_ints(a, b);
@@ -195,7 +209,7 @@ __device__ __forceinline__ typename C::PlaneT pair_term(const typename C::Pix &a
         if constexpr (C::DIST == EXACT) ang = angle32(r);
         else if constexpr (C::DIST == MINIMAX) ang = minimax32(r, xa, xb, q);
         else ang = chroma32(a, b, xa, xb);
-        if constexpr (C::FILTER == DDF) t = {ang, l2term32(a, b, r.d)};
+        if constexpr (C::FILTER == DDF) t = make_float2(ang, l2term32(a, b, r.d));
         else t = ang;
     }
     return t;
@@ -205,8 +219,10 @@ template <class C>
 __device__ __forceinline__ void add_term(typename C::PlaneT &x, const typename C::PlaneT &y)
 {
     if constexpr (C::FILTER == DDF) {
-        x.a += y.a;
-        x.l += y.l;
+        // two scalar adds: the packed FP32 add measured slower here (longer
+        // latency in these dependent sum chains, no throughput gain on GB300)
+        x.x += y.x;
+        x.y += y.y;
     } else {
         x += y;
     }
@@ -229,15 +245,15 @@ __device__ __forceinline__ void accumulate_row(const typename C::PlaneT *g, type
     }
 }
 
+// Terms of slice DYP: this thread's pixel p with partners p + (DYP, dx),
+// stored in the planes of the slice's buffer.
 template <class C, int DYP>
-__device__ __forceinline__ void slice(const typename C::Pix *pix, const Aux *aux, typename C::PlaneT *planes,
-                                      int tid, int cy, int cx, const typename C::Pix &self_px, const Aux &self_aux,
-                                      const typename C::PlaneT &self_term, typename C::PlaneT (*acc)[C::W], int q)
+__device__ __forceinline__ void slice_terms(const typename C::Pix *pix, const Aux *aux, typename C::PlaneT *planes,
+                                            int tid, int cy, int cx, const typename C::Pix &self_px,
+                                            const Aux &self_aux, int q)
 {
     constexpr int R = C::R, PXW = C::PXW, PLW = C::PLW, PLANE = C::PLH * C::PLW;
-    using PT = typename C::PlaneT;
     const int pc = (cy + 2 * R) * PLW + (cx + 2 * R);
-    // terms with partners p + (DYP, dx)
     if (tid < C::NC && cy + DYP < C::CH) {
         constexpr int K0 = (DYP == 0) ? 1 : -2 * R;
         constexpr int NK = (DYP == 0) ? 2 * R : 4 * R + 1;
@@ -250,7 +266,17 @@ __device__ __forceinline__ void slice(const typename C::Pix *pix, const Aux *aux
             planes[k * PLANE + pc] = pair_term<C>(self_px, pix[bi], self_aux, xb, q);
         }
     }
-    __syncthreads();
+}
+
+// Accumulation of slice DYP: p's own row (offset +DYP) and the mirrored row
+// (offset -DYP, terms written by the pixels above p).
+template <class C, int DYP>
+__device__ __forceinline__ void slice_acc(const typename C::PlaneT *planes, int tid, int cy, int cx,
+                                          const typename C::PlaneT &self_term, typename C::PlaneT (*acc)[C::W])
+{
+    constexpr int R = C::R, PLW = C::PLW, PLANE = C::PLH * C::PLW;
+    using PT = typename C::PlaneT;
+    const int pc = (cy + 2 * R) * PLW + (cx + 2 * R);
     if (tid < C::NC) {
         PT g[4 * R + 1];
         if constexpr (DYP == 0) {
@@ -273,49 +299,102 @@ __device__ __forceinline__ void slice(const typename C::Pix *pix, const Aux *aux
             accumulate_row<C, -DYP>(g, acc);
         }
     }
+}
+
+// One phase of the double-buffered slice pipeline: the terms of slice D+1
+// (other buffer) and the accumulation of slice D, then a barrier.
+template <class C, int D>
+__device__ __forceinline__ void slice_step(const typename C::Pix *pix, const Aux *aux, typename C::PlaneT *buf0,
+                                           typename C::PlaneT *buf1, int tid, int cy, int cx,
+                                           const typename C::Pix &self_px, const Aux &self_aux,
+                                           const typename C::PlaneT &self_term, typename C::PlaneT (*acc)[C::W], int q)
+{
+    if constexpr (D < 2 * C::R)
+        slice_terms<C, D + 1>(pix, aux, ((D + 1) & 1) ? buf1 : buf0, tid, cy, cx, self_px, self_aux, q);
+    slice_acc<C, D>((D & 1) ? buf1 : buf0, tid, cy, cx, self_term, acc);
     __syncthreads();
 }
 
 template <class C, int... D>
 __device__ __forceinline__ void all_slices(std::integer_sequence<int, D...>, const typename C::Pix *pix,
-                                           const Aux *aux, typename C::PlaneT *planes, int tid, int cy, int cx,
-                                           const typename C::Pix &self_px, const Aux &self_aux,
+                                           const Aux *aux, typename C::PlaneT *buf0, typename C::PlaneT *buf1, int tid,
+                                           int cy, int cx, const typename C::Pix &self_px, const Aux &self_aux,
                                            const typename C::PlaneT &self_term, typename C::PlaneT (*acc)[C::W],
                                            int q)
 {
-    (slice<C, D>(pix, aux, planes, tid, cy, cx, self_px, self_aux, self_term, acc, q), ...);
+    slice_terms<C, 0>(pix, aux, buf0, tid, cy, cx, self_px, self_aux, q);
+    __syncthreads();
+    (slice_step<C, D>(pix, aux, buf0, buf1, tid, cy, cx, self_px, self_aux, self_term, acc, q), ...);
 }
 
-// Step 4 of the tile: the member selection and the stores of one output pixel.
+// Step 4 of the tile, one thread per output pixel: the n scores of its window
+// from the raw aggregates (in place, rolled loops keep the code small), then
+// the member selection and the stores.
 template <class C>
 __device__ __forceinline__ void select_and_store(const TileParams &prm, int b, int x0, int y0, int tid,
-                                                 const typename C::Pix *pix, const typename C::HwT *hw)
+                                                 const typename C::Pix *pix, typename C::HwT *hw)
 {
     constexpr int R = C::R, W = C::W, NW = C::NW, PXW = C::PXW;
     using Pix = typename C::Pix;
     const int ty = tid / C::TW, tx = tid % C::TW;
     const int gy = y0 + ty, gx = x0 + tx;
     if (gy >= prm.M || gx >= prm.N) return;
-    const auto *f = hw + tid * NW;
+    const size_t lin = (size_t)gy * prm.N + gx;
+    auto *f = hw + tid * NW;
     int sel;
     if constexpr (C::FP64) {
-        sel = select64<C::FILTER, NW>(f);
+#pragma unroll 1
+        for (int k = 0; k < NW; ++k) {
+            double sa, sl = 0.0;
+            if constexpr (C::FILTER == DDF) {
+                sa = f[k].x;
+                sl = f[k].y;
+            } else {
+                sa = f[k];
+            }
+            if constexpr (C::FILTER == DDF && C::DIST == RGB)
+                sa = __fma_rn(kSlope64, sa, (double)NW * kOffset64);   // Eq. (10) summed over j
+            if (prm.agg) {
+                double *ag = prm.agg + (((size_t)b * prm.M * prm.N + lin) * NW + k) * 2;
+                ag[0] = sa;
+                ag[1] = sl;
+            }
+            const double sc = score64<C::FILTER>(sa, sl, prm.p);
+            if constexpr (C::FILTER == DDF) f[k].x = sc;
+            else f[k] = sc;
+        }
+        if constexpr (C::FILTER == DDF) sel = select64<C::FILTER, NW>([&](int k) { return f[k].x; });
+        else sel = select64<C::FILTER, NW>([&](int k) { return f[k]; });
     } else {
+        int quarter = -1;   // p = quarter / 4: the DDF score is Omega^4, else log2 Omega
+        if constexpr (C::FILTER == DDF) {
+            const float p4 = 4.0f * (float)prm.p;
+            if (p4 == rintf(p4)) quarter = (int)p4;
+        }
         float U = INFINITY, best = INFINITY;
         int arg = C::CENTRE;
-#pragma unroll
+#pragma unroll 1
         for (int k = 0; k < NW; ++k) {
-            const float2 v = f[k];
+            float sa = f[k].x;
+            if constexpr (C::FILTER == DDF && C::DIST == RGB) sa = fmaf(kSlope32, sa, (float)NW * kOffset32);
+            const float2 v = score32<R, C::FILTER, C::DIST>(sa, f[k].y, (float)prm.p, quarter);
+            f[k] = v;
+            if (prm.dbg_fe) {
+                float *d = prm.dbg_fe + (lin * NW + k) * 2;
+                d[0] = v.x;
+                d[1] = v.y;
+            }
             U = fminf(U, v.x + v.y);
             if (v.x < best) {
                 best = v.x;
                 arg = k;
             }
         }
+        if (prm.dbg_fe) return;   // the diagnostic wants the scores only
         int nnear = 0, first = -1;
         bool centre_near = false, equal = true, all_zero = true;
         float4 ref = make_float4(0, 0, 0, 0);
-#pragma unroll
+#pragma unroll 1
         for (int k = 0; k < NW; ++k) {
             const float2 v = f[k];
             if (v.x - v.y <= U) {
@@ -336,7 +415,7 @@ __device__ __forceinline__ void select_and_store(const TileParams &prm, int b, i
                     equal = equal && (same || coll);
                 }
                 const bool zero = (v.y == 0.0f) &&
-                                  ((C::FILTER == DDF && v.x == -INFINITY) ||
+                                  ((C::FILTER == DDF && (v.x == -INFINITY || v.x == 0.0f)) ||
                                    (C::FILTER == BVDF && C::DIST != MINIMAX && v.x == 0.0f));
                 all_zero = all_zero && zero;
                 centre_near = centre_near || (k == C::CENTRE);
@@ -350,11 +429,14 @@ __device__ __forceinline__ void select_and_store(const TileParams &prm, int b, i
         } else {
             // Members the FP64 path could still place in its tie set: the near
             // set widened by a margin of 100x the FP64 tie tolerance (1e-11,
-            // relative for BVDF, natural-log units for DDF).  Every other member
-            // is certified worse than the minimum by more than that margin.
-            const float delta = (C::FILTER == BVDF) ? 1e-9f * fmaxf(fabsf(U), 1e-3f) + 1e-12f : 1e-9f;
+            // relative for BVDF, natural-log units for DDF; the DDF score here
+            // is Omega^4 or log2 Omega).  Every other member is certified worse
+            // than the minimum by more than that margin.
+            const float delta = (C::FILTER == BVDF) ? 1e-9f * fmaxf(fabsf(U), 1e-3f) + 1e-12f
+                                : quarter >= 0   ? 4e-9f * fabsf(U)
+                                                 : 1e-9f;
             unsigned mask = 0;
-#pragma unroll
+#pragma unroll 1
             for (int k = 0; k < NW; ++k) {
                 const float2 v = f[k];
                 if (v.x - v.y <= U + delta) mask |= 1u << k;
@@ -366,7 +448,6 @@ __device__ __forceinline__ void select_and_store(const TileParams &prm, int b, i
         }
     }
     const Pix v = pix[(ty + sel / W) * PXW + (tx + sel % W) + 2 * R];
-    const size_t lin = (size_t)gy * prm.N + gx;
     if constexpr (C::F32IN) {
         const size_t plane = (size_t)prm.M * prm.N;
         float *o = (float *)prm.out + (size_t)b * 3 * plane + lin;
@@ -382,7 +463,6 @@ __device__ __forceinline__ void select_and_store(const TileParams &prm, int b, i
         if (prm.idx) prm.idx[lin] = (int8_t)sel;
     }
 }
-
 
 // Filters the tile with top-left output pixel (x0, y0) of image b.  Called
 // by all NTL >= C::NT threads of the block (every barrier is reached by all).
@@ -434,56 +514,38 @@ __device__ __forceinline__ void tile_body(const TileParams &prm, int b, int x0, 
     for (int i = 0; i < W; ++i)
 #pragma unroll
         for (int j = 0; j < W; ++j) acc[i][j] = PT{};
-    all_slices<C>(std::make_integer_sequence<int, 2 * R + 1>{}, pix, aux, planes, tid, cy, cx, self_px, self_aux,
-                  self_term, acc, prm.q);
+    all_slices<C>(std::make_integer_sequence<int, 2 * R + 1>{}, pix, aux, planes, planes + C::NPL * C::PLH * C::PLW,
+                  tid, cy, cx, self_px, self_aux, self_term, acc, prm.q);
 
-    // 3. scores, scattered to the windows of the tile
+    // 3. raw aggregates, scattered to the windows of the tile
     if (tid < C::NC) {
+        // windows q = p - e inside the tile and the image, as bit masks over ey and ex
+        unsigned vy = 0, vx = 0;
+#pragma unroll
+        for (int e = -R; e <= R; ++e) {
+            const int ty = cy - e - R, tx = cx - e - R;
+            if (ty >= 0 && ty < C::TH && y0 + ty < prm.M) vy |= 1u << (e + R);
+            if (tx >= 0 && tx < C::TW && x0 + tx < prm.N) vx |= 1u << (e + R);
+        }
 #pragma unroll
         for (int ey = -R; ey <= R; ++ey)
 #pragma unroll
             for (int ex = -R; ex <= R; ++ex) {
-                const int ty = cy - ey - R, tx = cx - ex - R;
-                const int gy = y0 + ty, gx = x0 + tx;
-                if (ty < 0 || ty >= C::TH || tx < 0 || tx >= C::TW || gy >= prm.M || gx >= prm.N) continue;
-                const int e = (ey + R) * W + (ex + R);
-                double sa, sl = 0.0;
-                if constexpr (C::FILTER == DDF) {
-                    sa = acc[ey + R][ex + R].a;
-                    sl = acc[ey + R][ex + R].l;
-                } else {
-                    sa = acc[ey + R][ex + R];
-                }
+                if (!((vy >> (ey + R)) & (vx >> (ex + R)) & 1u)) continue;
+                const int slot = ((cy - ey - R) * C::TW + (cx - ex - R)) * NW + (ey + R) * W + (ex + R);
                 if constexpr (C::FP64) {
-                    if constexpr (C::FILTER == DDF && C::DIST == RGB)
-                        sa = __fma_rn(kSlope64, sa, (double)NW * kOffset64);   // Eq. (10) summed over j
-                    hw[(ty * C::TW + tx) * NW + e] = score64<C::FILTER>(sa, sl, prm.p);
-                    if (prm.agg) {
-                        double *ag = prm.agg + (((size_t)b * prm.M * prm.N + (size_t)gy * prm.N + gx) * NW + e) * 2;
-                        ag[0] = sa;
-                        ag[1] = sl;
-                    }
+                    hw[slot] = acc[ey + R][ex + R];
+                } else if constexpr (C::FILTER == DDF) {
+                    hw[slot] = acc[ey + R][ex + R];
                 } else {
-                    float saf = (float)sa;
-                    if constexpr (C::FILTER == DDF && C::DIST == RGB)
-                        saf = fmaf(kSlope32, saf, (float)NW * kOffset32);
-                    const float2 fe = score32<R, C::FILTER, C::DIST>(saf, (float)sl, (float)prm.p);
-                    hw[(ty * C::TW + tx) * NW + e] = fe;
-                    if (prm.dbg_fe) {
-                        float *d = prm.dbg_fe + (((size_t)gy * prm.N + gx) * NW + e) * 2;
-                        d[0] = fe.x;
-                        d[1] = fe.y;
-                    }
+                    hw[slot] = make_float2(acc[ey + R][ex + R], 0.0f);
                 }
             }
     }
     __syncthreads();
 
-    // 4. selection, one thread per output pixel (skipped by the diagnostic
-    //    that only wants the scores)
-    bool selects = tid < C::TW * C::TH;
-    if constexpr (!C::FP64) selects = selects && !prm.dbg_fe;
-    if (selects) select_and_store<C>(prm, b, x0, y0, tid, pix, hw);
+    // 4. scores and selection, one thread per output pixel
+    if (tid < C::TW * C::TH) select_and_store<C>(prm, b, x0, y0, tid, pix, hw);
 }
 
 
@@ -596,7 +658,7 @@ __device__ __forceinline__ void recheck_pixel(const uint8_t *img, int M, int N, 
     }
     __syncwarp();
     if (lane == 0) {
-        const int sel = select64<FILTER, NW>(fs);
+        const int sel = select64<FILTER, NW>([&](int k) { return fs[k]; });
         const int4 v = px[sel];
         uint8_t *o = out + 3 * (size_t)lin;
         o[0] = (uint8_t)v.x;

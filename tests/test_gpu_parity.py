@@ -12,7 +12,7 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 DISTS = [("exact", 4), ("minimax", 4), ("minimax", 3), ("minimax", 2), ("rgb", 4)]
-FILTERS = [("bvdf", 0.5), ("ddf", 0.25), ("ddf", 0.5)]
+FILTERS = [("bvdf", 0.5), ("ddf", 0.25), ("ddf", 0.5), ("ddf", 0.3)]
 
 
 @pytest.fixture(scope="module")
@@ -84,7 +84,7 @@ def test_fp64_aggregates_match_oracle(V, O, win, filter, p, dist, q):
 
 
 @pytest.mark.parametrize("win", [3, 5])
-@pytest.mark.parametrize("filter,p", FILTERS + [("ddf", 0.0), ("ddf", 1.0)])
+@pytest.mark.parametrize("filter,p", FILTERS + [("ddf", 0.0), ("ddf", 1.0), ("ddf", 0.75), ("ddf", 0.9)])
 @pytest.mark.parametrize("dist,q", DISTS)
 def test_fp32_equals_fp64_larger(V, win, filter, p, dist, q):
     """Both precisions select the same member everywhere (512 x 512, 20% noise)."""
@@ -152,7 +152,7 @@ def test_full_size_1080p_sampled(V, O, filter, p, win):
 
 
 @pytest.mark.parametrize("win", [3, 5])
-@pytest.mark.parametrize("filter,p", [("bvdf", 0.5), ("ddf", 0.25), ("ddf", 0.5)])
+@pytest.mark.parametrize("filter,p", [("bvdf", 0.5), ("ddf", 0.25), ("ddf", 0.5), ("ddf", 0.3), ("ddf", 1.0)])
 @pytest.mark.parametrize("dist,q", [("exact", 4), ("minimax", 4), ("minimax", 3), ("rgb", 4)])
 def test_fp32_bounds_hold(V, win, filter, p, dist, q):
     """The FP32 scores lie within half their certified bound (the bound
@@ -163,15 +163,21 @@ def test_fp32_bounds_hold(V, win, filter, p, dist, q):
     fe = V.debug_fp32_scores(x, win, filter, p, dist, q).cpu().numpy().astype(np.float64)
     _, _, ag, _ = run(V, img, win, filter, p, dist, q, "fp64", agg=True)
     sa, sl = ag[..., 0], ag[..., 1]
+    a = 4 * p
     if filter == "bvdf":
-        f64 = sa
+        f64, zero = sa, None
+    elif a == round(a):                       # Omega^4 form
+        f64 = np.maximum(sa, 0) ** int(a) * sl ** (4 - int(a))
+        zero = 0.0
     else:
         with np.errstate(divide="ignore"):
             f64 = (p * np.log2(np.maximum(sa, 0)) if p > 0 else 0) + ((1 - p) * np.log2(sl) if p < 1 else 0)
+        zero = -np.inf
     f32, E = fe[..., 0], fe[..., 1]
     certain = np.isfinite(E)                  # Method 1 flags sums too close to 0 with E = inf
     finite = np.isfinite(f64) & certain
-    assert np.all(((f32 == -np.inf) == (f64 == -np.inf))[certain])
+    if zero is not None:
+        assert np.all(((f32 == zero) == (f64 == zero))[certain])
     err = np.abs(f32[finite] - f64[finite])
     assert np.all(err <= 0.5 * E[finite] + 1e-30), (err / np.maximum(E[finite], 1e-30)).max()
 
