@@ -183,7 +183,8 @@ __device__ __forceinline__ float cross2_32(const PairInts &r)
 __device__ __forceinline__ float angle32(const PairInts &r)
 {
     const float c2 = cross2_32(r);
-    const float m = fmaxf(c2 * r.Dh, 1e-30f);
+    // c2 * d^2 is 0 or >= 1 (integers), so adding 1e-30 only guards the zero
+    const float m = fmaf(c2, r.Dh, 1e-30f);
     const float rs = rsqrtf(m);
     const float ta = c2 * rs;     // sqrt(c2)/d = tan(theta)
     const float tb = r.Dh * rs;   // d/sqrt(c2) = cot(theta)
@@ -199,8 +200,8 @@ __device__ __forceinline__ float angle32(const PairInts &r)
 
 __device__ __forceinline__ float l2term32(const float4 a, const float4 b, float d)
 {
-    const float e = fmaf(-2.0f, d, a.w + b.w);   // |x - y|^2, exact
-    return e * rsqrtf(fmaxf(e, 1e-30f));          // relative error <= 5u
+    const float e = fmaf(-2.0f, d, a.w + b.w);   // |x - y|^2, exact (0 or >= 1)
+    return e * rsqrtf(e + 1e-30f);                // relative error <= 5u
 }
 
 __device__ __forceinline__ float horner4_32(const float *c, float t)

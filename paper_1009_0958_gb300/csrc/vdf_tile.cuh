@@ -142,9 +142,15 @@ __device__ __forceinline__ float2 score32(float sa, float sl, float p, int quart
         // p = a/4: Omega^4 = SA^a SL^(4-a) orders like Omega, with a relative
         // bound (a relA + (4-a) relL + 3 roundings) and no logarithm
         const float sa0 = fmaxf(sa, 0.0f);
-        float g = 1.0f;
-        for (int i = 0; i < quarter; ++i) g *= sa0;
-        for (int i = quarter; i < 4; ++i) g *= sl;
+        const float sa2 = sa0 * sa0, sl2 = sl * sl;
+        float g;   // at most three rounded products
+        switch (quarter) {
+        case 0: g = sl2 * sl2; break;
+        case 1: g = sa0 * (sl * sl2); break;
+        case 2: g = sa2 * sl2; break;
+        case 3: g = (sa0 * sa2) * sl; break;
+        default: g = sa2 * sa2; break;
+        }
         if (g == 0.0f) return make_float2(0.0f, 0.0f);   // an aggregate is exactly 0
         return make_float2(g, kSafety * g * (quarter * relA + (4 - quarter) * relL + 3.0f * kU));
     }
@@ -371,31 +377,47 @@ __device__ __forceinline__ void select_and_store(const TileParams &prm, int b, i
             const float p4 = 4.0f * (float)prm.p;
             if (p4 == rintf(p4)) quarter = (int)p4;
         }
-        float U = INFINITY, best = INFINITY;
-        int arg = C::CENTRE;
+        // one pass: U = min (f + E); the two smallest (f - E); the smallest f
+        float U = INFINITY, best = INFINITY, lo1 = INFINITY, lo2 = INFINITY;
+        int arg = C::CENTRE, arg1 = C::CENTRE;
+        const float pf = (float)prm.p;
 #pragma unroll 1
         for (int k = 0; k < NW; ++k) {
             float sa = f[k].x;
             if constexpr (C::FILTER == DDF && C::DIST == RGB) sa = fmaf(kSlope32, sa, (float)NW * kOffset32);
-            const float2 v = score32<R, C::FILTER, C::DIST>(sa, f[k].y, (float)prm.p, quarter);
+            const float2 v = score32<R, C::FILTER, C::DIST>(sa, f[k].y, pf, quarter);
             f[k] = v;
-            if (prm.dbg_fe) {
-                float *d = prm.dbg_fe + (lin * NW + k) * 2;
-                d[0] = v.x;
-                d[1] = v.y;
-            }
             U = fminf(U, v.x + v.y);
+            const float lo = v.x - v.y;
+            if (lo < lo1) {
+                lo2 = lo1;
+                lo1 = lo;
+                arg1 = k;
+            } else {
+                lo2 = fminf(lo2, lo);
+            }
             if (v.x < best) {
                 best = v.x;
                 arg = k;
             }
         }
-        if (prm.dbg_fe) return;   // the diagnostic wants the scores only
+        if (prm.dbg_fe) {   // the diagnostic wants the scores only
+#pragma unroll 1
+            for (int k = 0; k < NW; ++k) reinterpret_cast<float2 *>(prm.dbg_fe)[lin * NW + k] = f[k];
+            return;
+        }
+        // a single member can be minimal: the one with the smallest f - E
+        // (the member attaining U has f - E <= U, so it is that one)
+        const bool unique = lo2 > U;
         int nnear = 0, first = -1;
         bool centre_near = false, equal = true, all_zero = true;
         float4 ref = make_float4(0, 0, 0, 0);
+        if (unique) {
+            nnear = 1;
+            first = arg1;
+        }
 #pragma unroll 1
-        for (int k = 0; k < NW; ++k) {
+        for (int k = 0; k < (unique ? 0 : NW); ++k) {
             const float2 v = f[k];
             if (v.x - v.y <= U) {
                 const float4 xk = pix[(ty + k / W) * PXW + (tx + k % W) + 2 * R];
