@@ -240,14 +240,36 @@ template <class C, int DY>
 __device__ __forceinline__ void accumulate_row(const typename C::PlaneT *g, typename C::PlaneT (*acc)[C::W])
 {
     constexpr int R = C::R;
+    using PT = typename C::PlaneT;
+    if constexpr (!C::FP64 && R == 2) {
+        // FP32, 5x5: the five window sums share pair sums (18 adds, depth 3)
+        PT pr[8];
 #pragma unroll
-    for (int ex = -R; ex <= R; ++ex) {
-        typename C::PlaneT rs = g[2 * R + (-R - ex)];
+        for (int j = 0; j < 8; ++j) {
+            pr[j] = g[j];
+            add_term<C>(pr[j], g[j + 1]);
+        }
 #pragma unroll
-        for (int dx = -R - ex + 1; dx <= R - ex; ++dx) add_term<C>(rs, g[2 * R + dx]);
+        for (int ex = -R; ex <= R; ++ex) {
+            const int j = R - ex;   // the window covers g[j .. j + 4]
+            PT rs = pr[j];
+            add_term<C>(rs, pr[j + 2]);
+            add_term<C>(rs, g[j + 4]);
 #pragma unroll
-        for (int ey = -R; ey <= R; ++ey)
-            if (DY >= -R - ey && DY <= R - ey) add_term<C>(acc[ey + R][ex + R], rs);
+            for (int ey = -R; ey <= R; ++ey)
+                if (DY >= -R - ey && DY <= R - ey) add_term<C>(acc[ey + R][ex + R], rs);
+        }
+    } else {
+        // left to right (the FP64 recheck reproduces this order)
+#pragma unroll
+        for (int ex = -R; ex <= R; ++ex) {
+            PT rs = g[2 * R + (-R - ex)];
+#pragma unroll
+            for (int dx = -R - ex + 1; dx <= R - ex; ++dx) add_term<C>(rs, g[2 * R + dx]);
+#pragma unroll
+            for (int ey = -R; ey <= R; ++ey)
+                if (DY >= -R - ey && DY <= R - ey) add_term<C>(acc[ey + R][ex + R], rs);
+        }
     }
 }
 

@@ -337,3 +337,22 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+def fp32_pass(img: torch.Tensor, out: torch.Tensor, index: torch.Tensor, workspace: torch.Tensor, win=5,
+              filter="ddf", p=0.25, dist="exact", q=4, stream=None):
+    """Stage 1 of the FP32 path (certified pass + recheck list in `workspace`)."""
+    M, N = int(img.shape[0]), int(img.shape[1])
+    wp, wn = _aligned(workspace)
+    _check(lib().vdf_fp32_pass(_ptr(img), M, N, win, _code(FILTERS, filter), float(p), _code(DISTS, dist), q,
+                               _ptr(out), _ptr(index), wp, wn, _stream(stream)))
+
+
+def fp64_recheck(img: torch.Tensor, out: torch.Tensor, index: torch.Tensor, workspace: torch.Tensor, win=5,
+                 filter="ddf", p=0.25, dist="exact", q=4, stream=None):
+    """Stage 2 of the FP32 path (FP64 recheck of the listed pixels); may run
+    on another stream than stage 1 once it has finished."""
+    M, N = int(img.shape[0]), int(img.shape[1])
+    wp, wn = _aligned(workspace)
+    _check(lib().vdf_fp64_recheck(_ptr(img), M, N, win, _code(FILTERS, filter), float(p), _code(DISTS, dist), q,
+                                  _ptr(out), _ptr(index), wp, wn, _stream(stream)))

@@ -191,3 +191,29 @@ def test_host_buffer_path_equals_device_path(V):
     ih = torch.empty(img.shape[:2], dtype=torch.int8).pin_memory()
     V.filter_host(h, 5, "ddf", 0.25, "exact", 4, "fp32", oh, ih)
     assert np.array_equal(oh.numpy(), o_dev) and np.array_equal(ih.numpy(), i_dev)
+
+
+def test_two_stream_pipeline_equals_sequential(V):
+    """The two stages on two streams with alternating workspaces (the FP64
+    recheck of frame i overlapping the FP32 pass of frame i+1) give exactly
+    the single-call results."""
+    from paper_1009_0958_gb300 import synth
+    frames = [torch.from_numpy(synth.make_image(400, 640, 60 + k, 0.15, rectangles=8)[1]).cuda() for k in range(6)]
+    ref = [V.filter(f, 5, "ddf", 0.25, precision="fp32") for f in frames]
+    outs = [torch.empty_like(f) for f in frames]
+    idxs = [torch.empty(f.shape[:2], dtype=torch.int8, device="cuda") for f in frames]
+    ws = [V.alloc_workspace(400, 640, "fp32") for _ in range(2)]
+    main, side = torch.cuda.current_stream(), torch.cuda.Stream()
+    done = [torch.cuda.Event() for _ in frames]
+    for k, f in enumerate(frames):
+        if k >= 2:
+            main.wait_event(done[k - 2])
+        V.fp32_pass(f, outs[k], idxs[k], ws[k % 2], 5, "ddf", 0.25, stream=main)
+        passed = torch.cuda.Event()
+        passed.record(main)
+        side.wait_event(passed)
+        V.fp64_recheck(f, outs[k], idxs[k], ws[k % 2], 5, "ddf", 0.25, stream=side)
+        done[k].record(side)
+    torch.cuda.synchronize()
+    for k in range(len(frames)):
+        assert torch.equal(outs[k], ref[k][0]) and torch.equal(idxs[k], ref[k][1])
