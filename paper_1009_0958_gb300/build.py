@@ -25,6 +25,14 @@ COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler",
 # extra flags per translation unit; every csrc/*.cu is compiled
 UNIT_FLAGS = {
     "vdf_fp64.cu": ["-fmad=false"],
+    # FP32 tile kernels: no denormal can occur (integer-valued data; every
+    # guarded quantity is 0 or >= 1e-30), so flush-to-zero drops the denormal
+    # fix-ups around rsqrtf/__log2f
+    "vdf_fp32_s0.cu": ["-ftz=true"],
+    "vdf_fp32_s1.cu": ["-ftz=true"],
+    "vdf_fp32_s2.cu": ["-ftz=true"],
+    "vdf_fp32_s3.cu": ["-ftz=true"],
+    "vdf_batch.cu": ["-ftz=true"],
 }
 
 

@@ -70,11 +70,13 @@ struct TileCfg {
                                           float2>::type;
     static constexpr size_t PIX_BYTES = sizeof(Pix) * CH * PXW;
     static constexpr size_t AUX_BYTES = AUX ? (sizeof(Aux) * CH * PXW + 15) / 16 * 16 : 0;
+    // FP32: packed RGB key per pixel for the identical-vector test
+    static constexpr size_t KEY_BYTES = !FP64 ? (sizeof(unsigned) * CH * PXW + 15) / 16 * 16 : 0;
     static constexpr size_t PLANE_BYTES = sizeof(PlaneT) * NPL * PLH * PLW;
     static constexpr size_t HW_BYTES = sizeof(HwT) * TW * TH * NW;
     // two plane buffers (slice pipeline), later reused for the per-window scores
     static constexpr size_t UNION_BYTES = 2 * PLANE_BYTES > HW_BYTES ? 2 * PLANE_BYTES : HW_BYTES;
-    static constexpr size_t SMEM = PIX_BYTES + AUX_BYTES + UNION_BYTES;
+    static constexpr size_t SMEM = PIX_BYTES + AUX_BYTES + KEY_BYTES + UNION_BYTES;
 };
 
 // ------------------------------------------------------------ scores ------
@@ -113,12 +115,36 @@ __device__ __forceinline__ int select64(F f)
 // u = 2^-24) of the aggregates: angle 16 + 4R (terms + two summation
 // stages), chromaticity 11 + 4R (+2 for Eq. (10)), L2 6 + 4R; Method 1 has
 // an absolute bound 24u per term plus 4R u |SA|.  Bounds are doubled.
+// Omega^4 = SA^a SL^(4-a) for p = a/4, with at most three rounded products.
+template <int A>
+__device__ __forceinline__ float pow4_product(float sa0, float sl)
+{
+    const float sa2 = sa0 * sa0, sl2 = sl * sl;
+    if constexpr (A == 0) return sl2 * sl2;
+    else if constexpr (A == 1) return sa0 * (sl * sl2);
+    else if constexpr (A == 2) return sa2 * sl2;
+    else if constexpr (A == 3) return (sa0 * sa2) * sl;
+    else return sa2 * sa2;
+}
+
+constexpr float kSafety = 2.0f;   // factor applied to every analytic FP32 bound
+
+// Relative bound of Omega^4 for the exact and chromaticity modes (the
+// angular and L2 aggregate bounds of score32 below, a of them and 4 - a).
+template <int R, int DIST>
+__device__ __forceinline__ float pow4_erel(int a)
+{
+    constexpr float S = 4.0f * R;
+    constexpr float relA = (DIST == RGB ? 13.0f + S : 16.0f + S) * kU;
+    constexpr float relL = (6.0f + S) * kU;
+    return kSafety * (a * relA + (4 - a) * relL + 3.0f * kU);
+}
+
 template <int R, int FILTER, int DIST>
 __device__ __forceinline__ float2 score32(float sa, float sl, float p, int quarter)
 {
     constexpr int NW = (2 * R + 1) * (2 * R + 1);
     constexpr float S = 4.0f * R;
-    constexpr float kSafety = 2.0f;
     if (FILTER == BVDF) {
         float E;
         if (DIST == EXACT) E = (16.0f + S) * kU * sa;
@@ -142,16 +168,16 @@ __device__ __forceinline__ float2 score32(float sa, float sl, float p, int quart
         // p = a/4: Omega^4 = SA^a SL^(4-a) orders like Omega, with a relative
         // bound (a relA + (4-a) relL + 3 roundings) and no logarithm
         const float sa0 = fmaxf(sa, 0.0f);
-        const float sa2 = sa0 * sa0, sl2 = sl * sl;
-        float g;   // at most three rounded products
+        float g;
         switch (quarter) {
-        case 0: g = sl2 * sl2; break;
-        case 1: g = sa0 * (sl * sl2); break;
-        case 2: g = sa2 * sl2; break;
-        case 3: g = (sa0 * sa2) * sl; break;
-        default: g = sa2 * sa2; break;
+        case 0: g = pow4_product<0>(sa0, sl); break;
+        case 1: g = pow4_product<1>(sa0, sl); break;
+        case 2: g = pow4_product<2>(sa0, sl); break;
+        case 3: g = pow4_product<3>(sa0, sl); break;
+        default: g = pow4_product<4>(sa0, sl); break;
         }
         if (g == 0.0f) return make_float2(0.0f, 0.0f);   // an aggregate is exactly 0
+        if constexpr (DIST != MINIMAX) return make_float2(g, g * pow4_erel<R, DIST>(quarter));
         return make_float2(g, kSafety * g * (quarter * relA + (4 - quarter) * relL + 3.0f * kU));
     }
     constexpr float kLg2Abs = 1.6e-7f;   // __log2f on [1,2): 2^-22.6
@@ -355,30 +381,31 @@ __device__ __forceinline__ void all_slices(std::integer_sequence<int, D...>, con
     (slice_step<C, D>(pix, aux, buf0, buf1, tid, cy, cx, self_px, self_aux, self_term, acc, q), ...);
 }
 
-// Step 4 of the tile, one thread per output pixel: the n scores of its window
-// from the raw aggregates (in place, rolled loops keep the code small), then
-// the member selection and the stores.
-template <class C>
-__device__ __forceinline__ void select_and_store(const TileParams &prm, int b, int x0, int y0, int tid,
-                                                 const typename C::Pix *pix, typename C::HwT *hw)
+// Step 4a of the tile: the score of every (window, member) slot of the tile
+// from its raw aggregates, in place, spread over all threads of the block.
+template <class C, int NTL>
+__device__ __forceinline__ void score_slots(const TileParams &prm, int b, int x0, int y0, int tid,
+                                            typename C::HwT *hw)
 {
-    constexpr int R = C::R, W = C::W, NW = C::NW, PXW = C::PXW;
-    using Pix = typename C::Pix;
-    const int ty = tid / C::TW, tx = tid % C::TW;
-    const int gy = y0 + ty, gx = x0 + tx;
-    if (gy >= prm.M || gx >= prm.N) return;
-    const size_t lin = (size_t)gy * prm.N + gx;
-    auto *f = hw + tid * NW;
-    int sel;
-    if constexpr (C::FP64) {
+    constexpr int R = C::R, NW = C::NW;
+    int quarter = -1;   // FP32 DDF with p = quarter / 4: the score is Omega^4, else log2 Omega
+    if constexpr (!C::FP64 && C::FILTER == DDF) {
+        const float p4 = 4.0f * (float)prm.p;
+        if (p4 == rintf(p4)) quarter = (int)p4;
+    }
 #pragma unroll 1
-        for (int k = 0; k < NW; ++k) {
+    for (int s = tid; s < C::TW * C::TH * NW; s += NTL) {
+        const int w = s / NW, k = s - w * NW;
+        const int gy = y0 + w / C::TW, gx = x0 + w % C::TW;
+        if (gy >= prm.M || gx >= prm.N) continue;
+        const size_t lin = (size_t)gy * prm.N + gx;
+        if constexpr (C::FP64) {
             double sa, sl = 0.0;
             if constexpr (C::FILTER == DDF) {
-                sa = f[k].x;
-                sl = f[k].y;
+                sa = hw[s].x;
+                sl = hw[s].y;
             } else {
-                sa = f[k];
+                sa = hw[s];
             }
             if constexpr (C::FILTER == DDF && C::DIST == RGB)
                 sa = __fma_rn(kSlope64, sa, (double)NW * kOffset64);   // Eq. (10) summed over j
@@ -388,107 +415,151 @@ __device__ __forceinline__ void select_and_store(const TileParams &prm, int b, i
                 ag[1] = sl;
             }
             const double sc = score64<C::FILTER>(sa, sl, prm.p);
-            if constexpr (C::FILTER == DDF) f[k].x = sc;
-            else f[k] = sc;
+            if constexpr (C::FILTER == DDF) hw[s].x = sc;
+            else hw[s] = sc;
+        } else {
+            float sa = hw[s].x;
+            if constexpr (C::FILTER == DDF && C::DIST == RGB) sa = fmaf(kSlope32, sa, (float)NW * kOffset32);
+            const float2 v = score32<R, C::FILTER, C::DIST>(sa, hw[s].y, (float)prm.p, quarter);
+            hw[s] = v;
+            if (prm.dbg_fe) reinterpret_cast<float2 *>(prm.dbg_fe)[lin * NW + k] = v;
         }
+    }
+}
+
+// Step 4b of the tile, one thread per output pixel: the member selection
+// from the window's scores (FP32: computed here, in registers, from the raw
+// aggregates) and the stores.
+template <class C>
+__device__ __forceinline__ void select_and_store(const TileParams &prm, int b, int x0, int y0, int tid,
+                                                 const typename C::Pix *pix, const unsigned *keys,
+                                                 const typename C::HwT *hw)
+{
+    constexpr int R = C::R, W = C::W, NW = C::NW, PXW = C::PXW;
+    using Pix = typename C::Pix;
+    const int ty = tid / C::TW, tx = tid % C::TW;
+    const int gy = y0 + ty, gx = x0 + tx;
+    if (gy >= prm.M || gx >= prm.N) return;
+    const size_t lin = (size_t)gy * prm.N + gx;
+    const auto *f = hw + tid * NW;
+    int sel;
+    if constexpr (C::FP64) {
         if constexpr (C::FILTER == DDF) sel = select64<C::FILTER, NW>([&](int k) { return f[k].x; });
         else sel = select64<C::FILTER, NW>([&](int k) { return f[k]; });
     } else {
-        int quarter = -1;   // p = quarter / 4: the DDF score is Omega^4, else log2 Omega
+        // the n scores (f, E) of the window, in registers
+        float2 v[NW];
+#pragma unroll
+        for (int k = 0; k < NW; ++k) v[k] = f[k];
+        int quarter = -1;
         if constexpr (C::FILTER == DDF) {
             const float p4 = 4.0f * (float)prm.p;
             if (p4 == rintf(p4)) quarter = (int)p4;
         }
-        // one pass: U = min (f + E); the two smallest (f - E); the smallest f
-        float U = INFINITY, best = INFINITY, lo1 = INFINITY, lo2 = INFINITY;
-        int arg = C::CENTRE, arg1 = C::CENTRE;
-        const float pf = (float)prm.p;
-#pragma unroll 1
-        for (int k = 0; k < NW; ++k) {
-            float sa = f[k].x;
-            if constexpr (C::FILTER == DDF && C::DIST == RGB) sa = fmaf(kSlope32, sa, (float)NW * kOffset32);
-            const float2 v = score32<R, C::FILTER, C::DIST>(sa, f[k].y, pf, quarter);
-            f[k] = v;
-            U = fminf(U, v.x + v.y);
-            const float lo = v.x - v.y;
-            if (lo < lo1) {
-                lo2 = lo1;
-                lo1 = lo;
-                arg1 = k;
+        if constexpr (C::FILTER == DDF && C::DIST != MINIMAX) {
+            if (quarter >= 0) {
+                // Omega^4 = SA^a SL^(4-a) with a relative bound: the uniform
+                // switch keeps each unrolled loop branch-free
+                const float erel = pow4_erel<R, C::DIST>(quarter);
+                auto fill = [&](auto a) {
+#pragma unroll
+                    for (int k = 0; k < NW; ++k) {
+                        float sa = v[k].x;
+                        if constexpr (C::DIST == RGB) sa = fmaf(kSlope32, sa, (float)NW * kOffset32);
+                        const float g = pow4_product<decltype(a)::value>(fmaxf(sa, 0.0f), v[k].y);
+                        v[k] = make_float2(g, g * erel);
+                    }
+                };
+                switch (quarter) {
+                case 0: fill(std::integral_constant<int, 0>{}); break;
+                case 1: fill(std::integral_constant<int, 1>{}); break;
+                case 2: fill(std::integral_constant<int, 2>{}); break;
+                case 3: fill(std::integral_constant<int, 3>{}); break;
+                default: fill(std::integral_constant<int, 4>{}); break;
+                }
             } else {
-                lo2 = fminf(lo2, lo);
+#pragma unroll
+                for (int k = 0; k < NW; ++k) {
+                    float sa = v[k].x;
+                    if constexpr (C::DIST == RGB) sa = fmaf(kSlope32, sa, (float)NW * kOffset32);
+                    v[k] = score32<R, C::FILTER, C::DIST>(sa, v[k].y, (float)prm.p, -1);
+                }
             }
-            if (v.x < best) {
-                best = v.x;
+        } else {
+#pragma unroll
+            for (int k = 0; k < NW; ++k) v[k] = score32<R, C::FILTER, C::DIST>(v[k].x, v[k].y, (float)prm.p, quarter);
+        }
+        // U = min (f + E); the near set {f - E <= U} holds every true minimiser
+        float U = v[0].x + v[0].y, best = v[0].x;
+        int arg = 0;
+#pragma unroll
+        for (int k = 1; k < NW; ++k) {
+            U = fminf(U, v[k].x + v[k].y);
+            if (v[k].x < best) {
+                best = v[k].x;
                 arg = k;
             }
         }
-        if (prm.dbg_fe) {   // the diagnostic wants the scores only
+        unsigned near = 0;
+#pragma unroll
+        for (int k = 0; k < NW; ++k) near |= (v[k].x - v[k].y <= U ? 1u : 0u) << k;
+        if (near == 0) near = 1u << arg;   // not reached: the member attaining U is near
+        const int first = __ffs(near) - 1;
+        if ((near & (near - 1)) == 0) {
+            sel = first;   // a single member can be minimal
+        } else {
+            // several members may be minimal: provably equal (identical
+            // vectors, collinear ones for BVDF, exact zeros) -> tie rule;
+            // otherwise the FP64 recheck decides
+            bool equal = true, all_zero = true;
+            const int ri = (ty + first / W) * PXW + (tx + first % W) + 2 * R;
+            const unsigned rkey = keys[ri];
+            const float4 ref = pix[ri];
 #pragma unroll 1
-            for (int k = 0; k < NW; ++k) reinterpret_cast<float2 *>(prm.dbg_fe)[lin * NW + k] = f[k];
-            return;
-        }
-        // a single member can be minimal: the one with the smallest f - E
-        // (the member attaining U has f - E <= U, so it is that one)
-        const bool unique = lo2 > U;
-        int nnear = 0, first = -1;
-        bool centre_near = false, equal = true, all_zero = true;
-        float4 ref = make_float4(0, 0, 0, 0);
-        if (unique) {
-            nnear = 1;
-            first = arg1;
-        }
-#pragma unroll 1
-        for (int k = 0; k < (unique ? 0 : NW); ++k) {
-            const float2 v = f[k];
-            if (v.x - v.y <= U) {
-                const float4 xk = pix[(ty + k / W) * PXW + (tx + k % W) + 2 * R];
-                if (first < 0) {
-                    first = k;
-                    ref = xk;
-                } else {
-                    const bool same = xk.x == ref.x && xk.y == ref.y && xk.z == ref.z;
-                    bool coll = false;
-                    if constexpr (C::FILTER == BVDF) {
+            for (unsigned m = near; m; m &= m - 1) {
+                const int k = __ffs(m) - 1;
+                const int ki = (ty + k / W) * PXW + (tx + k % W) + 2 * R;
+                bool same = keys[ki] == rkey;
+                if constexpr (C::FILTER == BVDF) {
+                    if (!same) {
                         // same direction: integer cross product is 0, both non-zero
+                        const float4 xk = pix[ki];
                         const float c0 = fmaf(xk.y, ref.z, -(xk.z * ref.y));
                         const float c1 = fmaf(xk.z, ref.x, -(xk.x * ref.z));
                         const float c2 = fmaf(xk.x, ref.y, -(xk.y * ref.x));
-                        coll = c0 == 0.0f && c1 == 0.0f && c2 == 0.0f && xk.w > 0.0f && ref.w > 0.0f;
+                        same = c0 == 0.0f && c1 == 0.0f && c2 == 0.0f && xk.w > 0.0f && ref.w > 0.0f;
                     }
-                    equal = equal && (same || coll);
                 }
-                const bool zero = (v.y == 0.0f) &&
-                                  ((C::FILTER == DDF && (v.x == -INFINITY || v.x == 0.0f)) ||
-                                   (C::FILTER == BVDF && C::DIST != MINIMAX && v.x == 0.0f));
-                all_zero = all_zero && zero;
-                centre_near = centre_near || (k == C::CENTRE);
-                ++nnear;
+                equal = equal && same;
             }
-        }
-        if (nnear == 1) {
-            sel = first;
-        } else if (equal || all_zero) {
-            sel = centre_near ? C::CENTRE : first;
-        } else {
-            // Members the FP64 path could still place in its tie set: the near
-            // set widened by a margin of 100x the FP64 tie tolerance (1e-11,
-            // relative for BVDF, natural-log units for DDF; the DDF score here
-            // is Omega^4 or log2 Omega).  Every other member is certified worse
-            // than the minimum by more than that margin.
-            const float delta = (C::FILTER == BVDF) ? 1e-9f * fmaxf(fabsf(U), 1e-3f) + 1e-12f
-                                : quarter >= 0   ? 4e-9f * fabsf(U)
-                                                 : 1e-9f;
-            unsigned mask = 0;
-#pragma unroll 1
+            // exact zeros: f == 0 (or -inf) with a zero bound
+#pragma unroll
             for (int k = 0; k < NW; ++k) {
-                const float2 v = f[k];
-                if (v.x - v.y <= U + delta) mask |= 1u << k;
+                const bool zero = (v[k].y == 0.0f) &&
+                                  ((C::FILTER == DDF && (v[k].x == -INFINITY || v[k].x == 0.0f)) ||
+                                   (C::FILTER == BVDF && C::DIST != MINIMAX && v[k].x == 0.0f));
+                if ((near >> k) & 1u) all_zero = all_zero && zero;
             }
-            sel = arg;
-            const unsigned slot = atomicAdd(prm.recheck_ctr, 1u);
-            if (slot < prm.recheck_cap) prm.recheck_list[slot] = make_int2(prm.pix_base + gy * prm.N + gx, (int)mask);
-            else atomicOr(prm.recheck_ctr + 1, 1u);
+            if (equal || all_zero) {
+                sel = ((near >> C::CENTRE) & 1u) ? C::CENTRE : first;
+            } else {
+                // Members the FP64 path could still place in its tie set: the
+                // near set widened by a margin of 100x the FP64 tie tolerance
+                // (1e-11, relative for BVDF, natural-log units for DDF; the DDF
+                // score here is Omega^4 or log2 Omega).  Every other member is
+                // certified worse than the minimum by more than that margin.
+                const float delta = (C::FILTER == BVDF) ? 1e-9f * fmaxf(fabsf(U), 1e-3f) + 1e-12f
+                                    : quarter >= 0   ? 4e-9f * fabsf(U)
+                                                     : 1e-9f;
+                unsigned mask = 0;
+#pragma unroll
+                for (int k = 0; k < NW; ++k) mask |= (v[k].x - v[k].y <= U + delta ? 1u : 0u) << k;
+                sel = arg;
+                const unsigned slot = atomicAdd(prm.recheck_ctr, 1u);
+                if (slot < prm.recheck_cap)
+                    prm.recheck_list[slot] = make_int2(prm.pix_base + gy * prm.N + gx, (int)mask);
+                else atomicOr(prm.recheck_ctr + 1, 1u);
+            }
         }
     }
     const Pix v = pix[(ty + sel / W) * PXW + (tx + sel % W) + 2 * R];
@@ -518,8 +589,9 @@ __device__ __forceinline__ void tile_body(const TileParams &prm, int b, int x0, 
     using Pix = typename C::Pix;
     Pix *pix = reinterpret_cast<Pix *>(smem);
     Aux *aux = reinterpret_cast<Aux *>(smem + C::PIX_BYTES);
-    PT *planes = reinterpret_cast<PT *>(smem + C::PIX_BYTES + C::AUX_BYTES);
-    typename C::HwT *hw = reinterpret_cast<typename C::HwT *>(smem + C::PIX_BYTES + C::AUX_BYTES);
+    unsigned *keys = reinterpret_cast<unsigned *>(smem + C::PIX_BYTES + C::AUX_BYTES);
+    PT *planes = reinterpret_cast<PT *>(smem + C::PIX_BYTES + C::AUX_BYTES + C::KEY_BYTES);
+    typename C::HwT *hw = reinterpret_cast<typename C::HwT *>(smem + C::PIX_BYTES + C::AUX_BYTES + C::KEY_BYTES);
 
     const int tid = threadIdx.x;
 
@@ -528,6 +600,7 @@ __device__ __forceinline__ void tile_body(const TileParams &prm, int b, int x0, 
         const int r = i / PXW, c = i % PXW;
         const Pix v = load_pixel<C>(prm, b, y0 - R + r, x0 - 3 * R + c);
         pix[i] = v;
+        if constexpr (!C::FP64) keys[i] = (unsigned)v.x | ((unsigned)v.y << 8) | ((unsigned)v.z << 16);
         if constexpr (C::AUX) {
             Aux a;
             if constexpr (C::DIST == MINIMAX) {
@@ -588,8 +661,18 @@ __device__ __forceinline__ void tile_body(const TileParams &prm, int b, int x0, 
     }
     __syncthreads();
 
-    // 4. scores and selection, one thread per output pixel
-    if (tid < C::TW * C::TH) select_and_store<C>(prm, b, x0, y0, tid, pix, hw);
+    // 4. FP64 (and the FP32 diagnostic): scores of all slots (all threads);
+    //    then the selection, one thread per output pixel (the FP32 selection
+    //    scores its own window in registers)
+    bool score_all = C::FP64;
+    if constexpr (!C::FP64) score_all = prm.dbg_fe != nullptr;
+    if (score_all) {
+        score_slots<C, NTL>(prm, b, x0, y0, tid, hw);
+        __syncthreads();
+    }
+    bool selects = tid < C::TW * C::TH;
+    if constexpr (!C::FP64) selects = selects && !prm.dbg_fe;
+    if (selects) select_and_store<C>(prm, b, x0, y0, tid, pix, keys, hw);
 }
 
 
