@@ -464,9 +464,9 @@ __device__ __forceinline__ void select_and_store(const TileParams &prm, int b, i
                 auto fill = [&](auto a) {
 #pragma unroll
                     for (int k = 0; k < NW; ++k) {
-                        float sa = v[k].x;
+                        float sa = v[k].x;   // >= 0 in these modes (sums of non-negative terms)
                         if constexpr (C::DIST == RGB) sa = fmaf(kSlope32, sa, (float)NW * kOffset32);
-                        const float g = pow4_product<decltype(a)::value>(fmaxf(sa, 0.0f), v[k].y);
+                        const float g = pow4_product<decltype(a)::value>(sa, v[k].y);
                         v[k] = make_float2(g, g * erel);
                     }
                 };
@@ -490,20 +490,13 @@ __device__ __forceinline__ void select_and_store(const TileParams &prm, int b, i
             for (int k = 0; k < NW; ++k) v[k] = score32<R, C::FILTER, C::DIST>(v[k].x, v[k].y, (float)prm.p, quarter);
         }
         // U = min (f + E); the near set {f - E <= U} holds every true minimiser
-        float U = v[0].x + v[0].y, best = v[0].x;
-        int arg = 0;
+        float U = v[0].x + v[0].y;
 #pragma unroll
-        for (int k = 1; k < NW; ++k) {
-            U = fminf(U, v[k].x + v[k].y);
-            if (v[k].x < best) {
-                best = v[k].x;
-                arg = k;
-            }
-        }
+        for (int k = 1; k < NW; ++k) U = fminf(U, v[k].x + v[k].y);
         unsigned near = 0;
 #pragma unroll
         for (int k = 0; k < NW; ++k) near |= (v[k].x - v[k].y <= U ? 1u : 0u) << k;
-        if (near == 0) near = 1u << arg;   // not reached: the member attaining U is near
+        if (near == 0) near = 1u << C::CENTRE;   // not reached: the member attaining U is near
         const int first = __ffs(near) - 1;
         if ((near & (near - 1)) == 0) {
             sel = first;   // a single member can be minimal
@@ -552,8 +545,16 @@ __device__ __forceinline__ void select_and_store(const TileParams &prm, int b, i
                                     : quarter >= 0   ? 4e-9f * fabsf(U)
                                                      : 1e-9f;
                 unsigned mask = 0;
+                float best = v[0].x;
+                int arg = 0;   // provisional choice, replaced by the recheck
 #pragma unroll
-                for (int k = 0; k < NW; ++k) mask |= (v[k].x - v[k].y <= U + delta ? 1u : 0u) << k;
+                for (int k = 0; k < NW; ++k) {
+                    mask |= (v[k].x - v[k].y <= U + delta ? 1u : 0u) << k;
+                    if (v[k].x < best) {
+                        best = v[k].x;
+                        arg = k;
+                    }
+                }
                 sel = arg;
                 const unsigned slot = atomicAdd(prm.recheck_ctr, 1u);
                 if (slot < prm.recheck_cap)
