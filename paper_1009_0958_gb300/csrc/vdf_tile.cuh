@@ -504,34 +504,38 @@ __device__ __forceinline__ void select_and_store(const TileParams &prm, int b, i
             // several members may be minimal: provably equal (identical
             // vectors, collinear ones for BVDF, exact zeros) -> tie rule;
             // otherwise the FP64 recheck decides
-            bool equal = true, all_zero = true;
-            const int ri = (ty + first / W) * PXW + (tx + first % W) + 2 * R;
-            const unsigned rkey = keys[ri];
-            const float4 ref = pix[ri];
+            const int base = ty * PXW + tx + 2 * R;   // member 0 of the window
+            const unsigned rkey = keys[base + (first / W) * PXW + first % W];
+            unsigned same = 0;
+#pragma unroll
+            for (int k = 0; k < NW; ++k) same |= (keys[base + (k / W) * PXW + k % W] == rkey ? 1u : 0u) << k;
+            bool equal = (near & ~same) == 0;
+            if constexpr (C::FILTER == BVDF) {
+                if (!equal) {
+                    // same direction: integer cross product is 0, both non-zero
+                    const float4 ref = pix[base + (first / W) * PXW + first % W];
+                    equal = true;
 #pragma unroll 1
-            for (unsigned m = near; m; m &= m - 1) {
-                const int k = __ffs(m) - 1;
-                const int ki = (ty + k / W) * PXW + (tx + k % W) + 2 * R;
-                bool same = keys[ki] == rkey;
-                if constexpr (C::FILTER == BVDF) {
-                    if (!same) {
-                        // same direction: integer cross product is 0, both non-zero
-                        const float4 xk = pix[ki];
+                    for (unsigned m = near & ~same; m; m &= m - 1) {
+                        const int k = __ffs(m) - 1;
+                        const float4 xk = pix[base + (k / W) * PXW + k % W];
                         const float c0 = fmaf(xk.y, ref.z, -(xk.z * ref.y));
                         const float c1 = fmaf(xk.z, ref.x, -(xk.x * ref.z));
                         const float c2 = fmaf(xk.x, ref.y, -(xk.y * ref.x));
-                        same = c0 == 0.0f && c1 == 0.0f && c2 == 0.0f && xk.w > 0.0f && ref.w > 0.0f;
+                        equal = equal && c0 == 0.0f && c1 == 0.0f && c2 == 0.0f && xk.w > 0.0f && ref.w > 0.0f;
                     }
                 }
-                equal = equal && same;
             }
-            // exact zeros: f == 0 (or -inf) with a zero bound
+            bool all_zero = !equal;
+            if (!equal) {
+                // exact zeros: f == 0 (or -inf) with a zero bound
 #pragma unroll
-            for (int k = 0; k < NW; ++k) {
-                const bool zero = (v[k].y == 0.0f) &&
-                                  ((C::FILTER == DDF && (v[k].x == -INFINITY || v[k].x == 0.0f)) ||
-                                   (C::FILTER == BVDF && C::DIST != MINIMAX && v[k].x == 0.0f));
-                if ((near >> k) & 1u) all_zero = all_zero && zero;
+                for (int k = 0; k < NW; ++k) {
+                    const bool zero = (v[k].y == 0.0f) &&
+                                      ((C::FILTER == DDF && (v[k].x == -INFINITY || v[k].x == 0.0f)) ||
+                                       (C::FILTER == BVDF && C::DIST != MINIMAX && v[k].x == 0.0f));
+                    if ((near >> k) & 1u) all_zero = all_zero && zero;
+                }
             }
             if (equal || all_zero) {
                 sel = ((near >> C::CENTRE) & 1u) ? C::CENTRE : first;
