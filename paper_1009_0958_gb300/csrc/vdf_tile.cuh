@@ -72,11 +72,26 @@ struct TileCfg {
     static constexpr size_t AUX_BYTES = AUX ? (sizeof(Aux) * CH * PXW + 15) / 16 * 16 : 0;
     // FP32: packed RGB key per pixel for the identical-vector test
     static constexpr size_t KEY_BYTES = !FP64 ? (sizeof(unsigned) * CH * PXW + 15) / 16 * 16 : 0;
-    static constexpr size_t PLANE_BYTES = sizeof(PlaneT) * NPL * PLH * PLW;
+    // FP64: padded planes (PLH x PLW each).  FP32: planes packed with stride
+    // NC (entry = thread index); reads for pixels outside C land in the
+    // neighbouring plane, the preceding arrays or a 4R-entry tail and only
+    // feed windows outside the tile
+    static constexpr int PSTRIDE = FP64 ? PLH * PLW : NC;
+    static constexpr int PBUF = FP64 ? NPL * PLH * PLW : NPL * NC + 4 * R;
+    static constexpr size_t PLANE_BYTES = sizeof(PlaneT) * PBUF;
     static constexpr size_t HW_BYTES = sizeof(HwT) * TW * TH * NW;
-    // two plane buffers (slice pipeline), later reused for the per-window scores
-    static constexpr size_t UNION_BYTES = 2 * PLANE_BYTES > HW_BYTES ? 2 * PLANE_BYTES : HW_BYTES;
+    // two plane buffers (slice pipeline); FP64 reuses them for the per-window
+    // slots afterwards, FP32 writes each slot as soon as its aggregate is final
+    static constexpr size_t PLANES2_BYTES = (2 * PLANE_BYTES + 15) / 16 * 16;
+    static constexpr size_t HW_OFFSET = FP64 ? 0 : PLANES2_BYTES;
+    static constexpr size_t UNION_BYTES =
+        FP64 ? (2 * PLANE_BYTES > HW_BYTES ? 2 * PLANE_BYTES : HW_BYTES) : PLANES2_BYTES + HW_BYTES;
     static constexpr size_t SMEM = PIX_BYTES + AUX_BYTES + KEY_BYTES + UNION_BYTES;
+    static_assert(FP64 || PIX_BYTES >= sizeof(PlaneT) * (2 * R * CW + 2 * R), "FP32 plane reads stay in the block");
+    // CTAs per SM the register budget is sized for: two when two fit in the
+    // SM's 228 KB of shared memory (1 KB reserved per CTA) with at least 64
+    // registers per thread, so one CTA's barrier waits overlap the other's work
+    static constexpr int MINB = (2 * (SMEM + 1024) <= 228 * 1024 && 2 * NT * 64 <= 65536) ? 2 : 1;
 };
 
 // ------------------------------------------------------------ scores ------
@@ -381,6 +396,187 @@ __device__ __forceinline__ void all_slices(std::integer_sequence<int, D...>, con
     (slice_step<C, D>(pix, aux, buf0, buf1, tid, cy, cx, self_px, self_aux, self_term, acc, q), ...);
 }
 
+// ------------------------------------------------ FP32 slice pipeline ----
+// The FP32 path keeps the same slices but not the FP64 summation order (its
+// bounds need only the depth of each sum).  A thread keeps the terms of its
+// own row offset +D in registers and forms their window sums at once; only
+// the mirrored row -D passes through shared memory.  The row window sums H(DY)
+// reach the 2R+1 vertical window sums through shared partial sums (vstep32),
+// in the arrival order +1, 0, +2, -1, ..., +2R, -(2R-1), -2R.  Depth of an
+// aggregate: R = 2: 3 (pair sums) + 4; R = 1: 2 + 2; at most 4R either way.
+
+template <class C>
+__device__ __forceinline__ typename C::PlaneT psum(typename C::PlaneT a, const typename C::PlaneT &b)
+{
+    add_term<C>(a, b);
+    return a;
+}
+
+// Window sums of one row offset: h[ex + R] = sum of g[2R + dx], dx = -R-ex .. R-ex.
+template <class C>
+__device__ __forceinline__ void hsum32(const typename C::PlaneT *g, typename C::PlaneT *h)
+{
+    constexpr int R = C::R;
+    using PT = typename C::PlaneT;
+    if constexpr (R == 2) {
+        PT pr[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) pr[j] = psum<C>(g[j], g[j + 1]);
+#pragma unroll
+        for (int ex = -R; ex <= R; ++ex) h[ex + R] = psum<C>(psum<C>(pr[R - ex], pr[R - ex + 2]), g[R - ex + 4]);
+    } else {
+#pragma unroll
+        for (int ex = -R; ex <= R; ++ex) h[ex + R] = psum<C>(psum<C>(g[R - ex], g[R - ex + 1]), g[R - ex + 2]);
+    }
+}
+
+// Row offset DY arrives with its window sums h[ex]: update the partial sums
+// st; emit(ey, ex, A) receives each aggregate A = sum of H(ey + j), |j| <= R,
+// as soon as it is complete.
+template <class C, int DY, class Emit>
+__device__ __forceinline__ void vstep32(typename C::PlaneT (*st)[C::W], const typename C::PlaneT *h, Emit &emit)
+{
+#pragma unroll
+    for (int x = 0; x < C::W; ++x) {
+        const int ex = x - C::R;
+        if constexpr (C::R == 1) {
+            // st0 = H0+H1, st1 = H0 (+H-1)
+            if constexpr (DY == 1) st[0][x] = h[x];
+            else if constexpr (DY == 0) {
+                st[1][x] = h[x];
+                st[0][x] = psum<C>(st[0][x], h[x]);
+            } else if constexpr (DY == 2) emit(-1, ex, psum<C>(st[0][x], h[x]));
+            else if constexpr (DY == -1) {
+                emit(0, ex, psum<C>(st[0][x], h[x]));
+                st[1][x] = psum<C>(st[1][x], h[x]);
+            } else emit(1, ex, psum<C>(st[1][x], h[x]));
+        } else {
+            // st0 = H0+H1 (+H-1 +H-2), st1 = H0 (+H-1 +H-2 +H-3),
+            // st2 = H0+H1+H2 (+H3), st3 = H-1+H0+H1+H2
+            if constexpr (DY == 1) st[0][x] = h[x];
+            else if constexpr (DY == 0) {
+                st[1][x] = h[x];
+                st[0][x] = psum<C>(st[0][x], h[x]);
+            } else if constexpr (DY == 2) st[2][x] = psum<C>(st[0][x], h[x]);
+            else if constexpr (DY == -1) {
+                st[3][x] = psum<C>(st[2][x], h[x]);
+                st[0][x] = psum<C>(st[0][x], h[x]);
+                st[1][x] = psum<C>(st[1][x], h[x]);
+            } else if constexpr (DY == 3) {
+                emit(-1, ex, psum<C>(st[3][x], h[x]));
+                st[2][x] = psum<C>(st[2][x], h[x]);
+            } else if constexpr (DY == -2) {
+                emit(0, ex, psum<C>(st[3][x], h[x]));
+                st[0][x] = psum<C>(st[0][x], h[x]);
+                st[1][x] = psum<C>(st[1][x], h[x]);
+            } else if constexpr (DY == 4) emit(-2, ex, psum<C>(st[2][x], h[x]));
+            else if constexpr (DY == -3) {
+                emit(1, ex, psum<C>(st[0][x], h[x]));
+                st[1][x] = psum<C>(st[1][x], h[x]);
+            } else emit(2, ex, psum<C>(st[1][x], h[x]));
+        }
+    }
+}
+
+// One phase of the FP32 pipeline: the terms of slice D+1 (stored, and summed
+// for this thread's own row at once), the mirrored row -D of slice D (row 0
+// for D = 0), then a barrier.
+template <class C, int D, class Emit>
+__device__ __forceinline__ void phase32(const typename C::Pix *pix, const Aux *aux, typename C::PlaneT *buf0,
+                                        typename C::PlaneT *buf1, int tid, int cy, int cx,
+                                        const typename C::Pix &self_px, const Aux &self_aux,
+                                        const typename C::PlaneT &self_term, const typename C::PlaneT *g0,
+                                        typename C::PlaneT (*st)[C::W], Emit &emit, int q)
+{
+    constexpr int R = C::R, W = C::W, NC = C::NC, PXW = C::PXW, CW = C::CW;
+    using PT = typename C::PlaneT;
+    if (tid < NC) {
+        if constexpr (D < 2 * R) {
+            constexpr int DYP = D + 1;
+            PT *pl = (DYP & 1) ? buf1 : buf0;
+            PT g[4 * R + 1], h[W];
+            if (cy + DYP < C::CH) {
+#pragma unroll
+                for (int k = 0; k <= 4 * R; ++k) {
+                    const int bi = (cy + DYP) * PXW + (cx + k);   // partner p + (DYP, k - 2R)
+                    Aux xb{};
+                    if constexpr (C::AUX) xb = aux[bi];
+                    g[k] = pair_term<C>(self_px, pix[bi], self_aux, xb, q);
+                    pl[k * NC + tid] = g[k];
+                }
+                hsum32<C>(g, h);
+            } else {
+                // partners below C: only windows outside the tile use this row
+#pragma unroll
+                for (int x = 0; x < W; ++x) h[x] = PT{};
+            }
+            vstep32<C, DYP>(st, h, emit);
+        }
+        const PT *pl = (D & 1) ? buf1 : buf0;
+        PT g[4 * R + 1], h[W];
+        if constexpr (D == 0) {
+            g[2 * R] = self_term;
+#pragma unroll
+            for (int dx = 1; dx <= 2 * R; ++dx) {
+                g[2 * R + dx] = g0[dx - 1];
+                g[2 * R - dx] = pl[(dx - 1) * NC + tid - dx];
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k <= 4 * R; ++k) {
+                const int dx = k - 2 * R;
+                g[k] = pl[(2 * R - dx) * NC + tid - D * CW + dx];
+            }
+        }
+        hsum32<C>(g, h);
+        vstep32<C, -D>(st, h, emit);
+    }
+    __syncthreads();
+}
+
+// The FP32 aggregates of this thread's pixel p, each written to its
+// (window, member) slot of hw when final (windows inside the tile and image).
+template <class C, int... D>
+__device__ __forceinline__ void all_slices32(std::integer_sequence<int, D...>, const TileParams &prm, int x0, int y0,
+                                             const typename C::Pix *pix, const Aux *aux, typename C::PlaneT *buf0,
+                                             typename C::PlaneT *buf1, typename C::HwT *hw, int tid, int cy, int cx,
+                                             const typename C::Pix &self_px, const Aux &self_aux,
+                                             const typename C::PlaneT &self_term, int q)
+{
+    constexpr int R = C::R, NC = C::NC, PXW = C::PXW;
+    using PT = typename C::PlaneT;
+    // slice 0: partners p + (0, dx), dx = 1 .. 2R
+    PT g0[2 * R];
+    if (tid < NC) {
+#pragma unroll
+        for (int dx = 1; dx <= 2 * R; ++dx) {
+            const int bi = cy * PXW + (cx + 2 * R + dx);
+            Aux xb{};
+            if constexpr (C::AUX) xb = aux[bi];
+            g0[dx - 1] = pair_term<C>(self_px, pix[bi], self_aux, xb, q);
+            buf0[(dx - 1) * NC + tid] = g0[dx - 1];
+        }
+    }
+    __syncthreads();
+    // windows q = p - e inside the tile and the image, as bit masks over ey and ex
+    unsigned vy = 0, vx = 0;
+#pragma unroll
+    for (int e = -R; e <= R; ++e) {
+        const int ty = cy - e - R, tx = cx - e - R;
+        if (ty >= 0 && ty < C::TH && y0 + ty < prm.M) vy |= 1u << (e + R);
+        if (tx >= 0 && tx < C::TW && x0 + tx < prm.N) vx |= 1u << (e + R);
+    }
+    auto emit = [&](int ey, int ex, const PT &a) {
+        if ((vy >> (ey + R)) & (vx >> (ex + R)) & 1u) {
+            const int slot = ((cy - ey - R) * C::TW + (cx - ex - R)) * C::NW + (ey + R) * C::W + (ex + R);
+            if constexpr (C::FILTER == DDF) hw[slot] = a;
+            else hw[slot] = make_float2(a, 0.0f);
+        }
+    };
+    PT st[2 * R][C::W];
+    (phase32<C, D>(pix, aux, buf0, buf1, tid, cy, cx, self_px, self_aux, self_term, g0, st, emit, q), ...);
+}
+
 // Step 4a of the tile: the score of every (window, member) slot of the tile
 // from its raw aggregates, in place, spread over all threads of the block.
 template <class C, int NTL>
@@ -427,6 +623,59 @@ __device__ __forceinline__ void score_slots(const TileParams &prm, int b, int x0
     }
 }
 
+// The member selected from the near set (the members that can still be
+// minimal), FP32 path.  A single near member is the minimum.  Several near
+// members that are provably equal (identical vectors; collinear non-zero
+// vectors for BVDF, whose scores depend on directions only; or all exact
+// zeros) are exact ties: the tie rule picks the centre, else the lowest
+// index.  Otherwise the pixel goes to the FP64 recheck list with the member
+// mask wide(), and the provisional choice is argmin().
+template <class C, class ZeroF, class WideF, class ArgF>
+__device__ __forceinline__ int resolve_near(unsigned near, const TileParams &prm, const typename C::Pix *pix,
+                                            const unsigned *keys, int ty, int tx, int gy, int gx, ZeroF zero,
+                                            WideF wide, ArgF argmin)
+{
+    constexpr int R = C::R, W = C::W, NW = C::NW, PXW = C::PXW;
+    if (near == 0) near = 1u << C::CENTRE;   // not reached: the member attaining the minimum is near
+    const int first = __ffs(near) - 1;
+    if ((near & (near - 1)) == 0) return first;
+    const int base = ty * PXW + tx + 2 * R;   // member 0 of the window
+    const unsigned rkey = keys[base + (first / W) * PXW + first % W];
+    unsigned same = 0;
+#pragma unroll
+    for (int k = 0; k < NW; ++k) same |= (keys[base + (k / W) * PXW + k % W] == rkey ? 1u : 0u) << k;
+    bool equal = (near & ~same) == 0;
+    if constexpr (C::FILTER == BVDF) {
+        if (!equal) {
+            // same direction: integer cross product is 0, both non-zero
+            const float4 ref = pix[base + (first / W) * PXW + first % W];
+            equal = true;
+#pragma unroll 1
+            for (unsigned m = near & ~same; m; m &= m - 1) {
+                const int k = __ffs(m) - 1;
+                const float4 xk = pix[base + (k / W) * PXW + k % W];
+                const float c0 = fmaf(xk.y, ref.z, -(xk.z * ref.y));
+                const float c1 = fmaf(xk.z, ref.x, -(xk.x * ref.z));
+                const float c2 = fmaf(xk.x, ref.y, -(xk.y * ref.x));
+                equal = equal && c0 == 0.0f && c1 == 0.0f && c2 == 0.0f && xk.w > 0.0f && ref.w > 0.0f;
+            }
+        }
+    }
+    if (!equal) {
+        bool all_zero = true;
+#pragma unroll
+        for (int k = 0; k < NW; ++k)
+            if ((near >> k) & 1u) all_zero = all_zero && zero(k);
+        equal = all_zero;
+    }
+    if (equal) return ((near >> C::CENTRE) & 1u) ? C::CENTRE : first;
+    const unsigned mask = wide();
+    const unsigned slot = atomicAdd(prm.recheck_ctr, 1u);
+    if (slot < prm.recheck_cap) prm.recheck_list[slot] = make_int2(prm.pix_base + gy * prm.N + gx, (int)mask);
+    else atomicOr(prm.recheck_ctr + 1, 1u);
+    return argmin();
+}
+
 // Step 4b of the tile, one thread per output pixel: the member selection
 // from the window's scores (FP32: computed here, in registers, from the raw
 // aggregates) and the stores.
@@ -447,124 +696,130 @@ __device__ __forceinline__ void select_and_store(const TileParams &prm, int b, i
         if constexpr (C::FILTER == DDF) sel = select64<C::FILTER, NW>([&](int k) { return f[k].x; });
         else sel = select64<C::FILTER, NW>([&](int k) { return f[k]; });
     } else {
-        // the n scores (f, E) of the window, in registers
-        float2 v[NW];
-#pragma unroll
-        for (int k = 0; k < NW; ++k) v[k] = f[k];
         int quarter = -1;
         if constexpr (C::FILTER == DDF) {
             const float p4 = 4.0f * (float)prm.p;
             if (p4 == rintf(p4)) quarter = (int)p4;
         }
-        if constexpr (C::FILTER == DDF && C::DIST != MINIMAX) {
-            if (quarter >= 0) {
-                // Omega^4 = SA^a SL^(4-a) with a relative bound: the uniform
-                // switch keeps each unrolled loop branch-free
-                const float erel = pow4_erel<R, C::DIST>(quarter);
-                auto fill = [&](auto a) {
+        if constexpr (C::FILTER == BVDF && C::DIST != MINIMAX) {
+            // Relative bounds (E = g * erel, g >= 0): the near set {g - E <= min (g + E)}
+            // is {g <= gmin (1 + erel) / (1 - erel)}.  The threshold is evaluated
+            // with five roundings (each <= u relative) and padded by 1 + 6u, so
+            // the set computed here contains the near set.
+            float g[NW];
+#pragma unroll
+            for (int k = 0; k < NW; ++k) g[k] = f[k].x;
+            constexpr float erel = kSafety * ((C::DIST == RGB ? 11.0f : 16.0f) + 4.0f * R) * kU;
+            float gmin = g[0];
+#pragma unroll
+            for (int k = 1; k < NW; ++k) gmin = fminf(gmin, g[k]);
+            const float up = 1.0f + 6.0f * kU;
+            const float thr = gmin * ((1.0f + erel) / (1.0f - erel)) * up;
+            unsigned near = 0;
+#pragma unroll
+            for (int k = 0; k < NW; ++k) near |= (g[k] <= thr ? 1u : 0u) << k;
+            sel = resolve_near<C>(
+                near, prm, pix, keys, ty, tx, gy, gx, [&](int k) { return g[k] == 0.0f; },
+                [&]() {
+                    // widened by 100x the FP64 tie tolerance (relative 1e-11, floor 1e-3)
+                    const float U = gmin * (1.0f + erel);
+                    const float thw = (U + 1e-9f * fmaxf(U, 1e-3f) + 1e-12f) / (1.0f - erel) * up;
+                    unsigned mask = 0;
+#pragma unroll
+                    for (int k = 0; k < NW; ++k) mask |= (g[k] <= thw ? 1u : 0u) << k;
+                    return mask;
+                },
+                [&]() {
+                    // provisional choice (the recheck replaces it); the running
+                    // minimum keeps the scores in registers (no dynamic index)
+                    int arg = 0;
+                    float best = g[0];
+#pragma unroll
+                    for (int k = 1; k < NW; ++k)
+                        if (g[k] < best) {
+                            best = g[k];
+                            arg = k;
+                        }
+                    return arg;
+                });
+        } else {
+            // the n scores (f, E) of the window, in registers
+            float2 v[NW];
+#pragma unroll
+            for (int k = 0; k < NW; ++k) v[k] = f[k];
+            if constexpr (C::FILTER == DDF && C::DIST != MINIMAX) {
+                if (quarter >= 0) {
+                    // Omega^4 = SA^a SL^(4-a) with a relative bound: the uniform
+                    // switch keeps each unrolled loop branch-free
+                    const float erel = pow4_erel<R, C::DIST>(quarter);
+                    auto fill = [&](auto a) {
+#pragma unroll
+                        for (int k = 0; k < NW; ++k) {
+                            float sa = v[k].x;   // >= 0 in these modes (sums of non-negative terms)
+                            if constexpr (C::DIST == RGB) sa = fmaf(kSlope32, sa, (float)NW * kOffset32);
+                            const float g = pow4_product<decltype(a)::value>(sa, v[k].y);
+                            v[k] = make_float2(g, g * erel);
+                        }
+                    };
+                    switch (quarter) {
+                    case 0: fill(std::integral_constant<int, 0>{}); break;
+                    case 1: fill(std::integral_constant<int, 1>{}); break;
+                    case 2: fill(std::integral_constant<int, 2>{}); break;
+                    case 3: fill(std::integral_constant<int, 3>{}); break;
+                    default: fill(std::integral_constant<int, 4>{}); break;
+                    }
+                } else {
 #pragma unroll
                     for (int k = 0; k < NW; ++k) {
-                        float sa = v[k].x;   // >= 0 in these modes (sums of non-negative terms)
+                        float sa = v[k].x;
                         if constexpr (C::DIST == RGB) sa = fmaf(kSlope32, sa, (float)NW * kOffset32);
-                        const float g = pow4_product<decltype(a)::value>(sa, v[k].y);
-                        v[k] = make_float2(g, g * erel);
+                        v[k] = score32<R, C::FILTER, C::DIST>(sa, v[k].y, (float)prm.p, -1);
                     }
-                };
-                switch (quarter) {
-                case 0: fill(std::integral_constant<int, 0>{}); break;
-                case 1: fill(std::integral_constant<int, 1>{}); break;
-                case 2: fill(std::integral_constant<int, 2>{}); break;
-                case 3: fill(std::integral_constant<int, 3>{}); break;
-                default: fill(std::integral_constant<int, 4>{}); break;
                 }
             } else {
 #pragma unroll
-                for (int k = 0; k < NW; ++k) {
-                    float sa = v[k].x;
-                    if constexpr (C::DIST == RGB) sa = fmaf(kSlope32, sa, (float)NW * kOffset32);
-                    v[k] = score32<R, C::FILTER, C::DIST>(sa, v[k].y, (float)prm.p, -1);
-                }
+                for (int k = 0; k < NW; ++k)
+                    v[k] = score32<R, C::FILTER, C::DIST>(v[k].x, v[k].y, (float)prm.p, quarter);
             }
-        } else {
+            // U = min (f + E); the near set {f - E <= U} holds every true minimiser
+            float U = v[0].x + v[0].y;
 #pragma unroll
-            for (int k = 0; k < NW; ++k) v[k] = score32<R, C::FILTER, C::DIST>(v[k].x, v[k].y, (float)prm.p, quarter);
-        }
-        // U = min (f + E); the near set {f - E <= U} holds every true minimiser
-        float U = v[0].x + v[0].y;
+            for (int k = 1; k < NW; ++k) U = fminf(U, v[k].x + v[k].y);
+            unsigned near = 0;
 #pragma unroll
-        for (int k = 1; k < NW; ++k) U = fminf(U, v[k].x + v[k].y);
-        unsigned near = 0;
+            for (int k = 0; k < NW; ++k) near |= (v[k].x - v[k].y <= U ? 1u : 0u) << k;
+            sel = resolve_near<C>(
+                near, prm, pix, keys, ty, tx, gy, gx,
+                [&](int k) {
+                    // exact zeros: f == 0 (or -inf) with a zero bound
+                    return (v[k].y == 0.0f) && ((C::FILTER == DDF && (v[k].x == -INFINITY || v[k].x == 0.0f)) ||
+                                                (C::FILTER == BVDF && C::DIST != MINIMAX && v[k].x == 0.0f));
+                },
+                [&]() {
+                    // widened by 100x the FP64 tie tolerance (1e-11: relative for
+                    // BVDF, natural-log units for DDF, whose score here is Omega^4
+                    // or log2 Omega)
+                    const float delta = (C::FILTER == BVDF) ? 1e-9f * fmaxf(fabsf(U), 1e-3f) + 1e-12f
+                                        : quarter >= 0   ? 4e-9f * fabsf(U)
+                                                         : 1e-9f;
+                    unsigned mask = 0;
 #pragma unroll
-        for (int k = 0; k < NW; ++k) near |= (v[k].x - v[k].y <= U ? 1u : 0u) << k;
-        if (near == 0) near = 1u << C::CENTRE;   // not reached: the member attaining U is near
-        const int first = __ffs(near) - 1;
-        if ((near & (near - 1)) == 0) {
-            sel = first;   // a single member can be minimal
-        } else {
-            // several members may be minimal: provably equal (identical
-            // vectors, collinear ones for BVDF, exact zeros) -> tie rule;
-            // otherwise the FP64 recheck decides
-            const int base = ty * PXW + tx + 2 * R;   // member 0 of the window
-            const unsigned rkey = keys[base + (first / W) * PXW + first % W];
-            unsigned same = 0;
+                    for (int k = 0; k < NW; ++k) mask |= (v[k].x - v[k].y <= U + delta ? 1u : 0u) << k;
+                    return mask;
+                },
+                [&]() {
+                    // provisional choice (the recheck replaces it); the running
+                    // minimum keeps the scores in registers (no dynamic index)
+                    int arg = 0;
+                    float best = v[0].x;
 #pragma unroll
-            for (int k = 0; k < NW; ++k) same |= (keys[base + (k / W) * PXW + k % W] == rkey ? 1u : 0u) << k;
-            bool equal = (near & ~same) == 0;
-            if constexpr (C::FILTER == BVDF) {
-                if (!equal) {
-                    // same direction: integer cross product is 0, both non-zero
-                    const float4 ref = pix[base + (first / W) * PXW + first % W];
-                    equal = true;
-#pragma unroll 1
-                    for (unsigned m = near & ~same; m; m &= m - 1) {
-                        const int k = __ffs(m) - 1;
-                        const float4 xk = pix[base + (k / W) * PXW + k % W];
-                        const float c0 = fmaf(xk.y, ref.z, -(xk.z * ref.y));
-                        const float c1 = fmaf(xk.z, ref.x, -(xk.x * ref.z));
-                        const float c2 = fmaf(xk.x, ref.y, -(xk.y * ref.x));
-                        equal = equal && c0 == 0.0f && c1 == 0.0f && c2 == 0.0f && xk.w > 0.0f && ref.w > 0.0f;
-                    }
-                }
-            }
-            bool all_zero = !equal;
-            if (!equal) {
-                // exact zeros: f == 0 (or -inf) with a zero bound
-#pragma unroll
-                for (int k = 0; k < NW; ++k) {
-                    const bool zero = (v[k].y == 0.0f) &&
-                                      ((C::FILTER == DDF && (v[k].x == -INFINITY || v[k].x == 0.0f)) ||
-                                       (C::FILTER == BVDF && C::DIST != MINIMAX && v[k].x == 0.0f));
-                    if ((near >> k) & 1u) all_zero = all_zero && zero;
-                }
-            }
-            if (equal || all_zero) {
-                sel = ((near >> C::CENTRE) & 1u) ? C::CENTRE : first;
-            } else {
-                // Members the FP64 path could still place in its tie set: the
-                // near set widened by a margin of 100x the FP64 tie tolerance
-                // (1e-11, relative for BVDF, natural-log units for DDF; the DDF
-                // score here is Omega^4 or log2 Omega).  Every other member is
-                // certified worse than the minimum by more than that margin.
-                const float delta = (C::FILTER == BVDF) ? 1e-9f * fmaxf(fabsf(U), 1e-3f) + 1e-12f
-                                    : quarter >= 0   ? 4e-9f * fabsf(U)
-                                                     : 1e-9f;
-                unsigned mask = 0;
-                float best = v[0].x;
-                int arg = 0;   // provisional choice, replaced by the recheck
-#pragma unroll
-                for (int k = 0; k < NW; ++k) {
-                    mask |= (v[k].x - v[k].y <= U + delta ? 1u : 0u) << k;
-                    if (v[k].x < best) {
-                        best = v[k].x;
-                        arg = k;
-                    }
-                }
-                sel = arg;
-                const unsigned slot = atomicAdd(prm.recheck_ctr, 1u);
-                if (slot < prm.recheck_cap)
-                    prm.recheck_list[slot] = make_int2(prm.pix_base + gy * prm.N + gx, (int)mask);
-                else atomicOr(prm.recheck_ctr + 1, 1u);
-            }
+                    for (int k = 1; k < NW; ++k)
+                        if (v[k].x < best) {
+                            best = v[k].x;
+                            arg = k;
+                        }
+                    return arg;
+                });
         }
     }
     const Pix v = pix[(ty + sel / W) * PXW + (tx + sel % W) + 2 * R];
@@ -596,7 +851,8 @@ __device__ __forceinline__ void tile_body(const TileParams &prm, int b, int x0, 
     Aux *aux = reinterpret_cast<Aux *>(smem + C::PIX_BYTES);
     unsigned *keys = reinterpret_cast<unsigned *>(smem + C::PIX_BYTES + C::AUX_BYTES);
     PT *planes = reinterpret_cast<PT *>(smem + C::PIX_BYTES + C::AUX_BYTES + C::KEY_BYTES);
-    typename C::HwT *hw = reinterpret_cast<typename C::HwT *>(smem + C::PIX_BYTES + C::AUX_BYTES + C::KEY_BYTES);
+    typename C::HwT *hw =
+        reinterpret_cast<typename C::HwT *>(smem + C::PIX_BYTES + C::AUX_BYTES + C::KEY_BYTES + C::HW_OFFSET);
 
     const int tid = threadIdx.x;
 
@@ -631,40 +887,40 @@ __device__ __forceinline__ void tile_body(const TileParams &prm, int b, int x0, 
         if constexpr (C::AUX) self_aux = aux[own];
         self_term = pair_term<C>(self_px, self_px, self_aux, self_aux, prm.q);
     }
-    PT acc[W][W];
+    if constexpr (!C::FP64) {
+        // FP32: each slot is written inside the pipeline once its aggregate is final
+        all_slices32<C>(std::make_integer_sequence<int, 2 * R + 1>{}, prm, x0, y0, pix, aux, planes,
+                        planes + C::PBUF, hw, tid, cy, cx, self_px, self_aux, self_term, prm.q);
+    } else {
+        PT acc[W][W];
 #pragma unroll
-    for (int i = 0; i < W; ++i)
+        for (int i = 0; i < W; ++i)
 #pragma unroll
-        for (int j = 0; j < W; ++j) acc[i][j] = PT{};
-    all_slices<C>(std::make_integer_sequence<int, 2 * R + 1>{}, pix, aux, planes, planes + C::NPL * C::PLH * C::PLW,
-                  tid, cy, cx, self_px, self_aux, self_term, acc, prm.q);
+            for (int j = 0; j < W; ++j) acc[i][j] = PT{};
+        all_slices<C>(std::make_integer_sequence<int, 2 * R + 1>{}, pix, aux, planes, planes + C::PBUF, tid, cy, cx,
+                      self_px, self_aux, self_term, acc, prm.q);
 
-    // 3. raw aggregates, scattered to the windows of the tile
-    if (tid < C::NC) {
-        // windows q = p - e inside the tile and the image, as bit masks over ey and ex
-        unsigned vy = 0, vx = 0;
+        // 3. raw aggregates, scattered to the windows of the tile
+        if (tid < C::NC) {
+            // windows q = p - e inside the tile and the image, as bit masks over ey and ex
+            unsigned vy = 0, vx = 0;
 #pragma unroll
-        for (int e = -R; e <= R; ++e) {
-            const int ty = cy - e - R, tx = cx - e - R;
-            if (ty >= 0 && ty < C::TH && y0 + ty < prm.M) vy |= 1u << (e + R);
-            if (tx >= 0 && tx < C::TW && x0 + tx < prm.N) vx |= 1u << (e + R);
-        }
-#pragma unroll
-        for (int ey = -R; ey <= R; ++ey)
-#pragma unroll
-            for (int ex = -R; ex <= R; ++ex) {
-                if (!((vy >> (ey + R)) & (vx >> (ex + R)) & 1u)) continue;
-                const int slot = ((cy - ey - R) * C::TW + (cx - ex - R)) * NW + (ey + R) * W + (ex + R);
-                if constexpr (C::FP64) {
-                    hw[slot] = acc[ey + R][ex + R];
-                } else if constexpr (C::FILTER == DDF) {
-                    hw[slot] = acc[ey + R][ex + R];
-                } else {
-                    hw[slot] = make_float2(acc[ey + R][ex + R], 0.0f);
-                }
+            for (int e = -R; e <= R; ++e) {
+                const int ty = cy - e - R, tx = cx - e - R;
+                if (ty >= 0 && ty < C::TH && y0 + ty < prm.M) vy |= 1u << (e + R);
+                if (tx >= 0 && tx < C::TW && x0 + tx < prm.N) vx |= 1u << (e + R);
             }
+#pragma unroll
+            for (int ey = -R; ey <= R; ++ey)
+#pragma unroll
+                for (int ex = -R; ex <= R; ++ex) {
+                    if (!((vy >> (ey + R)) & (vx >> (ex + R)) & 1u)) continue;
+                    const int slot = ((cy - ey - R) * C::TW + (cx - ex - R)) * NW + (ey + R) * W + (ex + R);
+                    hw[slot] = acc[ey + R][ex + R];
+                }
+        }
+        __syncthreads();
     }
-    __syncthreads();
 
     // 4. FP64 (and the FP32 diagnostic): scores of all slots (all threads);
     //    then the selection, one thread per output pixel (the FP32 selection
@@ -682,7 +938,7 @@ __device__ __forceinline__ void tile_body(const TileParams &prm, int b, int x0, 
 
 
 template <class C>
-__global__ void __launch_bounds__(C::NT, 1) tile_kernel(const TileParams prm)
+__global__ void __launch_bounds__(C::NT, C::MINB) tile_kernel(const TileParams prm)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     tile_body<C, C::NT>(prm, blockIdx.z, blockIdx.x * C::TW, blockIdx.y * C::TH, smem);
