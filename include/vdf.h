@@ -250,6 +250,24 @@ void vdf_plan_destroy(vdf_plan *plan);
 int vdf_debug_fp32_scores(const uint8_t *img, int M, int N, int win, int filter, double p, int dist_mode,
                           int minimax_q, float *fe_out, void *stream);
 
+/*
+ * Diagnostic: the FP32 pair terms of n pixel pairs, exactly as the FP32 tile
+ * kernel computes them before summing (the paper defines the terms in
+ * Eq. (2) (arccos of the normalised inner product), Table 1 (Method 1,
+ * degree minimax_q) and Eq. (7) (Method 2); it has no such call).  The FP32
+ * path's certified bounds rest on these terms' error bounds: relative 16u
+ * (arccos), 11u (Method 2), absolute 24u (Method 1), relative 5u (|x - y|),
+ * u = 2^-24.
+ *   pairs      device, n x 6 ints: R, G, B of x then of y, each in [0, 255]
+ *              (other values give unspecified terms, never a fault)
+ *   angle_out  device, n floats, or NULL: the angular term of dist_mode
+ *   l2_out     device, n floats, or NULL: |x - y|
+ * Errors: VDF_E_INVALID for a null pairs pointer, n < 0, or a bad dist_mode
+ * or minimax_q; n = 0 launches nothing.  Asynchronous on stream.
+ */
+int vdf_debug_fp32_terms(const int *pairs, int n, int dist_mode, int minimax_q, float *angle_out, float *l2_out,
+                         void *stream);
+
 #ifdef __cplusplus
 }
 #endif

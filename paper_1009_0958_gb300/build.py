@@ -33,6 +33,7 @@ UNIT_FLAGS = {
     "vdf_fp32_s2.cu": ["-ftz=true"],
     "vdf_fp32_s3.cu": ["-ftz=true"],
     "vdf_batch.cu": ["-ftz=true"],
+    "vdf_debug.cu": ["-ftz=true"],
 }
 
 

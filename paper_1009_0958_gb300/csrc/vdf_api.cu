@@ -363,4 +363,12 @@ int vdf_debug_fp32_scores(const uint8_t *img, int M, int N, int win, int filter,
     return cuda_fail(vdf::run_fp32(prm, win / 2, filter, dist_mode, 0, (cudaStream_t)stream));
 }
 
+int vdf_debug_fp32_terms(const int *pairs, int n, int dist_mode, int minimax_q, float *angle_out, float *l2_out,
+                         void *stream)
+{
+    if (!pairs || n < 0 || dist_mode < VDF_DIST_EXACT || dist_mode > VDF_DIST_RGB) return VDF_E_INVALID;
+    if (dist_mode == VDF_DIST_MINIMAX && (minimax_q < 2 || minimax_q > 4)) return VDF_E_INVALID;
+    return cuda_fail(vdf::run_debug_terms(pairs, n, dist_mode, minimax_q, angle_out, l2_out, (cudaStream_t)stream));
+}
+
 }  // extern "C"

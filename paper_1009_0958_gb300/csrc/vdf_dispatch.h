@@ -24,4 +24,8 @@ cudaError_t run_backward(const float *gy, const int8_t *idx, float *gx, int B, i
 // FP64 recheck of the pixels listed by run_fp32.
 cudaError_t run_recheck(const RecheckParams &prm, int R, int filter, int dist, int blocks, cudaStream_t st);
 
+// FP32 pair terms of n pixel pairs (n x 6 ints), as the FP32 tile kernel computes them.
+cudaError_t run_debug_terms(const int *pairs, int n, int dist, int q, float *angle_out, float *l2_out,
+                            cudaStream_t st);
+
 }  // namespace vdf

@@ -55,8 +55,19 @@ constexpr float kHalfPi32 = 1.57079637f;           // nearest float to pi/2
 // atan(t) = t * Q(t^2) on [0, 1]: minimax fit for relative error (script
 // gen_atan_poly.py next to this file); float32 Horner evaluation error is
 // below 3.6 ulp of the result over the whole range.
-static __constant__ float kAtanQ[8] = {0.99999988f, -0.3333199f,    0.19969724f,  -0.14019482f,
-                                     0.099142946f, -0.059486423f, 0.02425243f,  -0.0046932846f};
+// Coefficient k as a constant expression (immediate operands, nothing
+// loaded from memory).
+__host__ __device__ constexpr float atan_q(int k)
+{
+    return k == 0   ? 0.99999988f
+           : k == 1 ? -0.3333199f
+           : k == 2 ? 0.19969724f
+           : k == 3 ? -0.14019482f
+           : k == 4 ? 0.099142946f
+           : k == 5 ? -0.059486423f
+           : k == 6 ? 0.02425243f
+                    : -0.0046932846f;
+}
 
 // ----------------------------------------------------- FP64 pair terms ----
 // Inputs are the integer RGB values of two pixels with n2 = |x|^2 in .w.
@@ -153,6 +164,22 @@ struct Aux {
     float a, b;   // Method 1: |x|, 1/|x| (0 for a zero vector); Method 2: sum x_k, |x|/sum x_k
 };
 
+// Per-pixel auxiliary values of the FP32 Method 1 / Method 2 terms; v holds
+// the integer RGB values with |x|^2 in .w.
+template <int DIST>
+__device__ __forceinline__ Aux make_aux(const float4 v)
+{
+    Aux a;
+    if constexpr (DIST == MINIMAX) {
+        a.a = sqrtf(v.w);
+        a.b = v.w > 0.0f ? 1.0f / a.a : 0.0f;
+    } else {
+        a.a = v.x + v.y + v.z;
+        a.b = a.a > 0.0f ? sqrtf(v.w) / a.a : 0.0f;
+    }
+    return a;
+}
+
 // Exact integer products split into hi + lo parts (Dekker via FMA):
 // P = |x|^2 |y|^2 and D = <x,y>^2, then c2 = P - D with one rounding.
 struct PairInts {
@@ -190,18 +217,25 @@ __device__ __forceinline__ float angle32(const PairInts &r)
     const float tb = r.Dh * rs;   // d/sqrt(c2) = cot(theta)
     const float t = fminf(ta, tb);
     const float s = t * t;
-    float v = kAtanQ[7];
+    float v = atan_q(7);
 #pragma unroll
-    for (int k = 6; k >= 0; --k) v = fmaf(v, s, kAtanQ[k]);
+    for (int k = 6; k >= 0; --k) v = fmaf(v, s, atan_q(k));
     const float a = t * v;
     // ta >= tb: theta >= 45 deg (also a zero vector: both 0, theta = pi/2)
     return (ta >= tb) ? (kHalfPi32 - a) : a;
 }
 
+// |x - y| in FP32.  e = |x - y|^2 is an exact integer in [0, 3 * 255^2]; on
+// that domain the approximate square root (one SFU operation) is within 2u
+// of the exact value (1.67u at worst; every attainable input is checked on
+// the GPU by the test suite through vdf_debug_fp32_terms) and exactly 0 at
+// 0.  Bound used: 5u.
 __device__ __forceinline__ float l2term32(const float4 a, const float4 b, float d)
 {
-    const float e = fmaf(-2.0f, d, a.w + b.w);   // |x - y|^2, exact (0 or >= 1)
-    return e * rsqrtf(e + 1e-30f);                // relative error <= 5u
+    const float e = fmaf(-2.0f, d, a.w + b.w);
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(e));
+    return r;
 }
 
 __device__ __forceinline__ float horner4_32(const float *c, float t)

@@ -862,17 +862,7 @@ __device__ __forceinline__ void tile_body(const TileParams &prm, int b, int x0, 
         const Pix v = load_pixel<C>(prm, b, y0 - R + r, x0 - 3 * R + c);
         pix[i] = v;
         if constexpr (!C::FP64) keys[i] = (unsigned)v.x | ((unsigned)v.y << 8) | ((unsigned)v.z << 16);
-        if constexpr (C::AUX) {
-            Aux a;
-            if constexpr (C::DIST == MINIMAX) {
-                a.a = sqrtf(v.w);
-                a.b = v.w > 0.0f ? 1.0f / a.a : 0.0f;
-            } else {
-                a.a = v.x + v.y + v.z;
-                a.b = a.a > 0.0f ? sqrtf(v.w) / a.a : 0.0f;
-            }
-            aux[i] = a;
-        }
+        if constexpr (C::AUX) aux[i] = make_aux<C::DIST>(v);
     }
     __syncthreads();
 

@@ -48,7 +48,9 @@ def lib():
             L.vdf_fp64_recheck.argtypes = [P, i, i, i, i, d, i, i, P, P, P, sz, P]
             L.vdf_workspace_stats.argtypes = [P, P, P, P]
             L.vdf_debug_fp32_scores.argtypes = [P, i, i, i, i, d, i, i, P, P]
+            L.vdf_debug_fp32_terms.argtypes = [P, i, i, i, P, P, P]
             for f in ("vdf_filter", "vdf_filter_host", "vdf_workspace_stats", "vdf_debug_fp32_scores",
+                      "vdf_debug_fp32_terms",
                       "vdf_fp32_pass", "vdf_fp64_recheck", "vdf_filter_f32", "vdf_backward_f32"):
                 getattr(L, f).restype = i
             _lib = L
@@ -155,6 +157,19 @@ def debug_fp32_scores(img: torch.Tensor, win=3, filter="bvdf", p=0.5, dist="exac
     _check(lib().vdf_debug_fp32_scores(_ptr(img.contiguous()), M, N, win, _code(FILTERS, filter), float(p),
                                        _code(DISTS, dist), q, _ptr(fe), _stream(stream)))
     return fe
+
+
+def debug_fp32_terms(pairs: torch.Tensor, dist="exact", q=4, stream=None):
+    """FP32 pair terms of the tile kernel for an (n, 6) int32 CUDA tensor of
+    pixel pairs (R, G, B of x then y).  Returns ``(angle, l2)`` float32."""
+    if not (pairs.is_cuda and pairs.dtype == torch.int32 and pairs.dim() == 2 and pairs.shape[1] == 6):
+        raise VdfError("pairs must be a CUDA int32 tensor of shape (n, 6)")
+    pairs = pairs.contiguous()
+    n = int(pairs.shape[0])
+    ang = torch.empty(n, dtype=torch.float32, device=pairs.device)
+    l2 = torch.empty(n, dtype=torch.float32, device=pairs.device)
+    _check(lib().vdf_debug_fp32_terms(_ptr(pairs), n, _code(DISTS, dist), q, _ptr(ang), _ptr(l2), _stream(stream)))
+    return ang, l2
 
 
 def filter_f32(img: torch.Tensor, win: int = 3, filter="ddf", p: float = 0.5, dist="exact", q: int = 4,

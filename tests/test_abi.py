@@ -55,3 +55,12 @@ def test_aliasing_and_workspace_checks(L):
     p = ctypes.c_void_p(0x10000)
     assert L.vdf_filter(p, 8, 8, 3, 0, 0.5, 0, 4, 0, p, None, None, None, 0, None) == -1      # out == img
     assert L.vdf_filter(p, 8, 8, 3, 0, 0.5, 0, 4, 1, ctypes.c_void_p(0x20000), None, None, None, 0, None) == -5
+
+
+def test_debug_terms_arguments_checked_on_host(L):
+    p = ctypes.c_void_p(0x10000)
+    assert L.vdf_debug_fp32_terms(None, 4, 0, 4, None, None, None) == -1
+    assert L.vdf_debug_fp32_terms(p, -1, 0, 4, None, None, None) == -1
+    assert L.vdf_debug_fp32_terms(p, 4, 3, 4, None, None, None) == -1
+    assert L.vdf_debug_fp32_terms(p, 4, 1, 5, None, None, None) == -1
+    assert L.vdf_debug_fp32_terms(p, 0, 0, 4, None, None, None) == 0    # nothing to launch
