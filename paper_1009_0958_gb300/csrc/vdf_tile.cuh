@@ -623,6 +623,34 @@ __device__ __forceinline__ void score_slots(const TileParams &prm, int b, int x0
     }
 }
 
+// Minimum of n values by a pairwise tree (depth log2 n instead of n - 1).
+template <int N>
+__device__ __forceinline__ float tree_min(const float *g)
+{
+    float m[N];
+#pragma unroll
+    for (int k = 0; k < N; ++k) m[k] = g[k];
+#pragma unroll
+    for (int w = 1; w < N; w *= 2)
+#pragma unroll
+        for (int k = 0; k + w < N; k += 2 * w) m[k] = fminf(m[k], m[k + w]);
+    return m[0];
+}
+
+// Bit k set where pred(k), combined by a pairwise tree of ORs.
+template <int N, class P>
+__device__ __forceinline__ unsigned bit_mask(P pred)
+{
+    unsigned m[N];
+#pragma unroll
+    for (int k = 0; k < N; ++k) m[k] = pred(k) ? (1u << k) : 0u;
+#pragma unroll
+    for (int w = 1; w < N; w *= 2)
+#pragma unroll
+        for (int k = 0; k + w < N; k += 2 * w) m[k] |= m[k + w];
+    return m[0];
+}
+
 // The member selected from the near set (the members that can still be
 // minimal), FP32 path.  A single near member is the minimum.  Several near
 // members that are provably equal (identical vectors; collinear non-zero
@@ -701,33 +729,54 @@ __device__ __forceinline__ void select_and_store(const TileParams &prm, int b, i
             const float p4 = 4.0f * (float)prm.p;
             if (p4 == rintf(p4)) quarter = (int)p4;
         }
-        if constexpr (C::FILTER == BVDF && C::DIST != MINIMAX) {
-            // Relative bounds (E = g * erel, g >= 0): the near set {g - E <= min (g + E)}
-            // is {g <= gmin (1 + erel) / (1 - erel)}.  The threshold is evaluated
-            // with five roundings (each <= u relative) and padded by 1 + 6u, so
-            // the set computed here contains the near set.
+        // Relative bounds (BVDF with the exact or chromaticity terms, and DDF
+        // with p = quarter / 4 scored by Omega^4): E = g * erel, g >= 0
+        bool relative = C::FILTER == BVDF && C::DIST != MINIMAX;
+        if constexpr (C::FILTER == DDF && C::DIST != MINIMAX) relative = quarter >= 0;
+        if (relative) {
             float g[NW];
+            float erel;
+            if constexpr (C::FILTER == BVDF) {
 #pragma unroll
-            for (int k = 0; k < NW; ++k) g[k] = f[k].x;
-            constexpr float erel = kSafety * ((C::DIST == RGB ? 11.0f : 16.0f) + 4.0f * R) * kU;
-            float gmin = g[0];
+                for (int k = 0; k < NW; ++k) g[k] = f[k].x;
+                erel = kSafety * ((C::DIST == RGB ? 11.0f : 16.0f) + 4.0f * R) * kU;
+            } else {
+                // the uniform switch keeps each unrolled loop branch-free
+                erel = pow4_erel<R, C::DIST>(quarter);
+                auto fill = [&](auto a) {
 #pragma unroll
-            for (int k = 1; k < NW; ++k) gmin = fminf(gmin, g[k]);
+                    for (int k = 0; k < NW; ++k) {
+                        float sa = f[k].x;   // >= 0 in these modes (sums of non-negative terms)
+                        if constexpr (C::DIST == RGB) sa = fmaf(kSlope32, sa, (float)NW * kOffset32);
+                        g[k] = pow4_product<decltype(a)::value>(sa, f[k].y);
+                    }
+                };
+                switch (quarter) {
+                case 0: fill(std::integral_constant<int, 0>{}); break;
+                case 1: fill(std::integral_constant<int, 1>{}); break;
+                case 2: fill(std::integral_constant<int, 2>{}); break;
+                case 3: fill(std::integral_constant<int, 3>{}); break;
+                default: fill(std::integral_constant<int, 4>{}); break;
+                }
+            }
+            // The near set {g - E <= min (g + E)} is {g <= gmin (1 + erel) / (1 - erel)}.
+            // The threshold is evaluated with five roundings (each <= u
+            // relative) and padded by 1 + 6u, so the set computed here
+            // contains the near set.
+            const float gmin = tree_min<NW>(g);
             const float up = 1.0f + 6.0f * kU;
             const float thr = gmin * ((1.0f + erel) / (1.0f - erel)) * up;
-            unsigned near = 0;
-#pragma unroll
-            for (int k = 0; k < NW; ++k) near |= (g[k] <= thr ? 1u : 0u) << k;
+            const unsigned near = bit_mask<NW>([&](int k) { return g[k] <= thr; });
             sel = resolve_near<C>(
                 near, prm, pix, keys, ty, tx, gy, gx, [&](int k) { return g[k] == 0.0f; },
                 [&]() {
-                    // widened by 100x the FP64 tie tolerance (relative 1e-11, floor 1e-3)
+                    // widened by 100x the FP64 tie tolerance (1e-11: relative
+                    // with floor 1e-3 for BVDF; in the log domain for DDF, a
+                    // relative 4e-11 on Omega^4)
                     const float U = gmin * (1.0f + erel);
-                    const float thw = (U + 1e-9f * fmaxf(U, 1e-3f) + 1e-12f) / (1.0f - erel) * up;
-                    unsigned mask = 0;
-#pragma unroll
-                    for (int k = 0; k < NW; ++k) mask |= (g[k] <= thw ? 1u : 0u) << k;
-                    return mask;
+                    const float delta = (C::FILTER == BVDF) ? 1e-9f * fmaxf(U, 1e-3f) + 1e-12f : 4e-9f * U;
+                    const float thw = (U + delta) / (1.0f - erel) * up;
+                    return bit_mask<NW>([&](int k) { return g[k] <= thw; });
                 },
                 [&]() {
                     // provisional choice (the recheck replaces it); the running
@@ -743,51 +792,21 @@ __device__ __forceinline__ void select_and_store(const TileParams &prm, int b, i
                     return arg;
                 });
         } else {
+            // general bounds (Method 1, and DDF with p not a multiple of 1/4):
             // the n scores (f, E) of the window, in registers
             float2 v[NW];
 #pragma unroll
-            for (int k = 0; k < NW; ++k) v[k] = f[k];
-            if constexpr (C::FILTER == DDF && C::DIST != MINIMAX) {
-                if (quarter >= 0) {
-                    // Omega^4 = SA^a SL^(4-a) with a relative bound: the uniform
-                    // switch keeps each unrolled loop branch-free
-                    const float erel = pow4_erel<R, C::DIST>(quarter);
-                    auto fill = [&](auto a) {
-#pragma unroll
-                        for (int k = 0; k < NW; ++k) {
-                            float sa = v[k].x;   // >= 0 in these modes (sums of non-negative terms)
-                            if constexpr (C::DIST == RGB) sa = fmaf(kSlope32, sa, (float)NW * kOffset32);
-                            const float g = pow4_product<decltype(a)::value>(sa, v[k].y);
-                            v[k] = make_float2(g, g * erel);
-                        }
-                    };
-                    switch (quarter) {
-                    case 0: fill(std::integral_constant<int, 0>{}); break;
-                    case 1: fill(std::integral_constant<int, 1>{}); break;
-                    case 2: fill(std::integral_constant<int, 2>{}); break;
-                    case 3: fill(std::integral_constant<int, 3>{}); break;
-                    default: fill(std::integral_constant<int, 4>{}); break;
-                    }
-                } else {
-#pragma unroll
-                    for (int k = 0; k < NW; ++k) {
-                        float sa = v[k].x;
-                        if constexpr (C::DIST == RGB) sa = fmaf(kSlope32, sa, (float)NW * kOffset32);
-                        v[k] = score32<R, C::FILTER, C::DIST>(sa, v[k].y, (float)prm.p, -1);
-                    }
-                }
-            } else {
-#pragma unroll
-                for (int k = 0; k < NW; ++k)
-                    v[k] = score32<R, C::FILTER, C::DIST>(v[k].x, v[k].y, (float)prm.p, quarter);
+            for (int k = 0; k < NW; ++k) {
+                float sa = f[k].x;
+                if constexpr (C::FILTER == DDF && C::DIST == RGB) sa = fmaf(kSlope32, sa, (float)NW * kOffset32);
+                v[k] = score32<R, C::FILTER, C::DIST>(sa, f[k].y, (float)prm.p, quarter);
             }
             // U = min (f + E); the near set {f - E <= U} holds every true minimiser
-            float U = v[0].x + v[0].y;
+            float hi[NW];
 #pragma unroll
-            for (int k = 1; k < NW; ++k) U = fminf(U, v[k].x + v[k].y);
-            unsigned near = 0;
-#pragma unroll
-            for (int k = 0; k < NW; ++k) near |= (v[k].x - v[k].y <= U ? 1u : 0u) << k;
+            for (int k = 0; k < NW; ++k) hi[k] = v[k].x + v[k].y;
+            const float U = tree_min<NW>(hi);
+            const unsigned near = bit_mask<NW>([&](int k) { return v[k].x - v[k].y <= U; });
             sel = resolve_near<C>(
                 near, prm, pix, keys, ty, tx, gy, gx,
                 [&](int k) {
@@ -802,10 +821,7 @@ __device__ __forceinline__ void select_and_store(const TileParams &prm, int b, i
                     const float delta = (C::FILTER == BVDF) ? 1e-9f * fmaxf(fabsf(U), 1e-3f) + 1e-12f
                                         : quarter >= 0   ? 4e-9f * fabsf(U)
                                                          : 1e-9f;
-                    unsigned mask = 0;
-#pragma unroll
-                    for (int k = 0; k < NW; ++k) mask |= (v[k].x - v[k].y <= U + delta ? 1u : 0u) << k;
-                    return mask;
+                    return bit_mask<NW>([&](int k) { return v[k].x - v[k].y <= U + delta; });
                 },
                 [&]() {
                     // provisional choice (the recheck replaces it); the running
@@ -856,13 +872,25 @@ __device__ __forceinline__ void tile_body(const TileParams &prm, int b, int x0, 
 
     const int tid = threadIdx.x;
 
-    // 1. pixels of C plus a 2R column margin on each side, edge-replicated
-    for (int i = tid; i < C::CH * PXW; i += NTL) {
-        const int r = i / PXW, c = i % PXW;
-        const Pix v = load_pixel<C>(prm, b, y0 - R + r, x0 - 3 * R + c);
-        pix[i] = v;
-        if constexpr (!C::FP64) keys[i] = (unsigned)v.x | ((unsigned)v.y << 8) | ((unsigned)v.z << 16);
-        if constexpr (C::AUX) aux[i] = make_aux<C::DIST>(v);
+    // 1. pixels of C plus a 2R column margin on each side, edge-replicated;
+    //    every load of a thread is issued before the first is used (one
+    //    memory round trip per tile)
+    {
+        constexpr int NP = C::CH * PXW, PER = (NP + NTL - 1) / NTL;
+        Pix v[PER];
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            const int i = tid + k * NTL;
+            if (i < NP) v[k] = load_pixel<C>(prm, b, y0 - R + i / PXW, x0 - 3 * R + i % PXW);
+        }
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            const int i = tid + k * NTL;
+            if (i >= NP) continue;
+            pix[i] = v[k];
+            if constexpr (!C::FP64) keys[i] = (unsigned)v[k].x | ((unsigned)v[k].y << 8) | ((unsigned)v[k].z << 16);
+            if constexpr (C::AUX) aux[i] = make_aux<C::DIST>(v[k]);
+        }
     }
     __syncthreads();
 
