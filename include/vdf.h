@@ -131,6 +131,33 @@ int vdf_filter_host(const uint8_t *img_host, int M, int N, int win, int filter, 
                     size_t dev_buffer_bytes, void *stream);
 
 /*
+ * A sequence of count host frames of equal size through vdf_filter, the
+ * copies of each frame overlapping the filtering of its neighbours (frames
+ * of a video; the paper filters one image at a time and has no such call).
+ * Two device slots of vdf_host_buffer_bytes(M, N, precision) each are used
+ * in turn; library-owned streams (four per device, created on first use)
+ * carry the upload, the FP32 pass (or the FP64 filter), the FP64 recheck and
+ * the download, ordered by events, so the upload of frame i + 1 and the
+ * download of frame i - 1 run while frame i is filtered.
+ *   img_host[i]        host, M*N*3 uint8 (HWC); pinned for overlap
+ *   out_host[i]        host, M*N*3 uint8
+ *   index_out_host     NULL, or an array whose entries are NULL or host M*N int8
+ *   dev_buffer         device, 256-byte aligned, vdf_host_frames_buffer_bytes(M, N,
+ *                      precision) bytes, owned by the caller
+ *   stream             the work starts after the work queued on it, and it waits
+ *                      for the last download; the call returns when every frame
+ *                      is on the host (also after an error)
+ * Errors: VDF_E_INVALID for bad sizes or null frame pointers (count = 0 is
+ * a no-op); VDF_E_WORKSPACE for a short or misaligned buffer; the filter's
+ * own errors (its argument checks run on the first frame); VDF_E_CUDA.
+ * Calls on one device are serialised by a lock.
+ */
+size_t vdf_host_frames_buffer_bytes(int M, int N, int precision);
+int vdf_filter_host_frames(const uint8_t *const *img_host, uint8_t *const *out_host, int8_t *const *index_out_host,
+                           int count, int M, int N, int win, int filter, double p, int dist_mode, int minimax_q,
+                           int precision, void *dev_buffer, size_t dev_buffer_bytes, void *stream);
+
+/*
  * Float32 batch variant (the differentiable path).  img: device, B x 3 x M x N
  * float32 (NCHW, any non-negative values, e.g. RGB in [0, 1]); out: same
  * shape; index_out: device, B x M x N int8 (may be NULL, but the backward

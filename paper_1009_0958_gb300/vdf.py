@@ -49,8 +49,10 @@ def lib():
             L.vdf_workspace_stats.argtypes = [P, P, P, P]
             L.vdf_debug_fp32_scores.argtypes = [P, i, i, i, i, d, i, i, P, P]
             L.vdf_debug_fp32_terms.argtypes = [P, i, i, i, P, P, P]
+            L.vdf_host_frames_buffer_bytes.argtypes, L.vdf_host_frames_buffer_bytes.restype = [i, i, i], sz
+            L.vdf_filter_host_frames.argtypes = [P, P, P, i, i, i, i, i, d, i, i, i, P, sz, P]
             for f in ("vdf_filter", "vdf_filter_host", "vdf_workspace_stats", "vdf_debug_fp32_scores",
-                      "vdf_debug_fp32_terms",
+                      "vdf_debug_fp32_terms", "vdf_filter_host_frames",
                       "vdf_fp32_pass", "vdf_fp64_recheck", "vdf_filter_f32", "vdf_backward_f32"):
                 getattr(L, f).restype = i
             _lib = L
@@ -148,6 +150,40 @@ def filter_host(img_host: torch.Tensor, win=3, filter="bvdf", p=0.5, dist="exact
     _check(lib().vdf_filter_host(_ptr(img_host), M, N, win, _code(FILTERS, filter), float(p), _code(DISTS, dist), q,
                                  prec, _ptr(out_host), _ptr(index_host), bp, bn, _stream(stream)))
     return out_host, index_host
+
+
+def host_frames_buffer_bytes(M: int, N: int, precision="fp32") -> int:
+    return int(lib().vdf_host_frames_buffer_bytes(M, N, _code(PRECISIONS, precision)))
+
+
+def filter_host_frames(frames, win=5, filter="ddf", p=0.25, dist="exact", q=4, precision="fp32", outs=None,
+                       indices=None, dev_buffer: torch.Tensor | None = None, stream=None):
+    """Filter a list of M x N x 3 uint8 host tensors (pinned for overlap)
+    with the copies of each frame overlapping the filtering of the others.
+    Returns ``(outs, indices)`` as lists of host tensors."""
+    if not frames:
+        return [], []
+    M, N = int(frames[0].shape[0]), int(frames[0].shape[1])
+    for f in frames:
+        if f.is_cuda or f.dtype != torch.uint8 or tuple(f.shape) != (M, N, 3) or not f.is_contiguous():
+            raise VdfError("frames must be contiguous host uint8 tensors of one shape (M, N, 3)")
+    n = len(frames)
+    if outs is None:
+        outs = [torch.empty((M, N, 3), dtype=torch.uint8).pin_memory() for _ in range(n)]
+    if indices is None:
+        indices = [torch.empty((M, N), dtype=torch.int8).pin_memory() for _ in range(n)]
+    prec = _code(PRECISIONS, precision)
+    need = int(lib().vdf_host_frames_buffer_bytes(M, N, prec))
+    if dev_buffer is None:
+        dev_buffer = torch.empty(need + 256, dtype=torch.uint8, device="cuda")
+    bp, bn = _aligned(dev_buffer)
+    P = ctypes.c_void_p
+    ins = (P * n)(*[f.data_ptr() for f in frames])
+    ous = (P * n)(*[o.data_ptr() for o in outs])
+    ixs = (P * n)(*[(x.data_ptr() if x is not None else None) for x in indices])
+    _check(lib().vdf_filter_host_frames(ins, ous, ixs, n, M, N, win, _code(FILTERS, filter), float(p),
+                                        _code(DISTS, dist), q, prec, bp, bn, _stream(stream)))
+    return outs, indices
 
 
 def debug_fp32_scores(img: torch.Tensor, win=3, filter="bvdf", p=0.5, dist="exact", q=4, stream=None):

@@ -64,3 +64,17 @@ def test_debug_terms_arguments_checked_on_host(L):
     assert L.vdf_debug_fp32_terms(p, 4, 3, 4, None, None, None) == -1
     assert L.vdf_debug_fp32_terms(p, 4, 1, 5, None, None, None) == -1
     assert L.vdf_debug_fp32_terms(p, 0, 0, 4, None, None, None) == 0    # nothing to launch
+
+
+def test_host_frames_arguments_checked_on_host(L):
+    p = ctypes.c_void_p(0x10000)
+    arr = (ctypes.c_void_p * 1)(p)
+    nul = (ctypes.c_void_p * 1)(None)
+    assert L.vdf_filter_host_frames(None, arr, None, 1, 8, 8, 3, 0, 0.5, 0, 4, 1, p, 1 << 20, None) == -1
+    assert L.vdf_filter_host_frames(arr, nul, None, 1, 8, 8, 3, 0, 0.5, 0, 4, 1, p, 1 << 20, None) == -1
+    assert L.vdf_filter_host_frames(arr, arr, None, -1, 8, 8, 3, 0, 0.5, 0, 4, 1, p, 1 << 20, None) == -1
+    assert L.vdf_filter_host_frames(arr, arr, None, 1, 0, 8, 3, 0, 0.5, 0, 4, 1, p, 1 << 20, None) == -1
+    assert L.vdf_filter_host_frames(arr, arr, None, 1, 8, 8, 3, 0, 0.5, 0, 4, 1, p, 16, None) == -5
+    assert L.vdf_filter_host_frames(arr, arr, None, 0, 8, 8, 3, 0, 0.5, 0, 4, 1, None, 0, None) == 0
+    one = L.vdf_host_buffer_bytes(8, 8, 1)
+    assert L.vdf_host_frames_buffer_bytes(8, 8, 1) == 2 * ((one + 255) // 256 * 256)
