@@ -134,11 +134,12 @@ int vdf_filter_host(const uint8_t *img_host, int M, int N, int win, int filter, 
  * A sequence of count host frames of equal size through vdf_filter, the
  * copies of each frame overlapping the filtering of its neighbours (frames
  * of a video; the paper filters one image at a time and has no such call).
- * Two device slots of vdf_host_buffer_bytes(M, N, precision) each are used
- * in turn; library-owned streams (four per device, created on first use)
- * carry the upload, the FP32 pass (or the FP64 filter), the FP64 recheck and
- * the download, ordered by events, so the upload of frame i + 1 and the
- * download of frame i - 1 run while frame i is filtered.
+ * Three device slots of vdf_host_buffer_bytes(M, N, precision) bytes
+ * (rounded up to 256) are used in turn; library-owned streams (four per
+ * device, created on first use) carry the upload, the FP32 pass (or the FP64
+ * filter), the FP64 recheck and the download, ordered by events, so the
+ * upload of frame i + 1 and the download of frame i - 1 run while frame i is
+ * filtered, and the recheck of frame i beside the next passes.
  *   img_host[i]        host, M*N*3 uint8 (HWC); pinned for overlap
  *   out_host[i]        host, M*N*3 uint8
  *   index_out_host     NULL, or an array whose entries are NULL or host M*N int8

@@ -2,14 +2,15 @@
 // the filter, with the copies of each frame overlapping the filtering of its
 // neighbours.
 //
-// Two device slots hold one frame each (input, output, index map and the
+// Three device slots hold one frame each (input, output, index map and the
 // filter's workspace).  Four library-owned streams per device carry the
 // stages: host-to-device copy, FP32 pass (or the whole FP64 filter), FP64
-// recheck, device-to-host copy.  Frame i uses slot i % 2; its upload waits
-// until the download of frame i - 2 (same slot) has finished, and every
+// recheck, device-to-host copy.  Frame i uses slot i % 3; its upload waits
+// until the download of frame i - 3 (same slot) has finished, and every
 // later stage waits for the one before it (events).  So the upload of frame
 // i + 1 and the download of frame i - 1 run while frame i is filtered, and
-// the recheck of frame i runs beside the FP32 pass of frame i + 1.
+// the recheck of frame i runs beside the FP32 passes of frames i + 1 and
+// i + 2 (with two slots the pass of frame i + 2 would wait for it).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -19,7 +20,7 @@
 
 namespace {
 
-constexpr int kSlots = 2;
+constexpr int kSlots = 3;
 constexpr int kMaxDevices = 64;
 
 struct Lanes {
@@ -104,7 +105,7 @@ int vdf_filter_host_frames(const uint8_t *const *img_host, uint8_t *const *out_h
         int8_t *idx_host = index_out_host ? index_out_host[i] : nullptr;
         int8_t *idx_dev = idx_host ? d_idx : nullptr;
 
-        if (i >= kSlots) e = cudaStreamWaitEvent(L->up, L->freed[k], 0);   // frame i - 2 is downloaded
+        if (i >= kSlots) e = cudaStreamWaitEvent(L->up, L->freed[k], 0);   // frame i - 3 is downloaded
         if (e == cudaSuccess) e = cudaMemcpyAsync(d_in, img_host[i], 3 * px, cudaMemcpyHostToDevice, L->up);
         if (e == cudaSuccess) e = cudaEventRecord(L->loaded[k], L->up);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(L->pass, L->loaded[k], 0);

@@ -77,4 +77,4 @@ def test_host_frames_arguments_checked_on_host(L):
     assert L.vdf_filter_host_frames(arr, arr, None, 1, 8, 8, 3, 0, 0.5, 0, 4, 1, p, 16, None) == -5
     assert L.vdf_filter_host_frames(arr, arr, None, 0, 8, 8, 3, 0, 0.5, 0, 4, 1, None, 0, None) == 0
     one = L.vdf_host_buffer_bytes(8, 8, 1)
-    assert L.vdf_host_frames_buffer_bytes(8, 8, 1) == 2 * ((one + 255) // 256 * 256)
+    assert L.vdf_host_frames_buffer_bytes(8, 8, 1) == 3 * ((one + 255) // 256 * 256)

@@ -1,5 +1,5 @@
 """vdf_filter_host_frames: a sequence of host frames, copies overlapped with
-filtering through two device slots, must give every frame exactly what
+filtering through three device slots, must give every frame exactly what
 vdf_filter gives it (and the oracle, on small frames)."""
 import numpy as np
 import pytest
