@@ -180,36 +180,34 @@ __device__ __forceinline__ Aux make_aux(const float4 v)
     return a;
 }
 
-// Exact integer products split into hi + lo parts (Dekker via FMA):
-// P = |x|^2 |y|^2 and D = <x,y>^2, then c2 = P - D with one rounding.
+// Integer quantities of a pixel pair.  d = <x,y> is exact (< 2^24).
+// D = d^2 is split hi + lo by FMA (Dekker: D = Dh + Dl exactly), and so is
+// P = |x|^2 |y|^2 (Ph + Pl; Method 1's branch test uses it).
+// c2 = |x x y|^2 = P - D (Lagrange) is fma(|x|^2, |y|^2, -Dh) - Dl: the FMA
+// gives the integer P - Dh exactly when it is below 2^24 (then c2 has one
+// rounding) and with relative error <= u otherwise, where c2 >= 2^24 - 2^11
+// dwarfs |Dl| <= 2^11: relative error <= 2u in every case.
 struct PairInts {
-    float d, Ph, Pl, Dh, Dl;
+    float d, Ph, Pl, Dh, Dl, c2;
 };
 
 __device__ __forceinline__ PairInts pair_ints(const float4 a, const float4 b)
 {
     PairInts r;
-    r.d = fmaf(a.z, b.z, fmaf(a.y, b.y, a.x * b.x));   // exact (< 2^24)
+    r.d = fmaf(a.z, b.z, fmaf(a.y, b.y, a.x * b.x));
     r.Ph = a.w * b.w;
     r.Pl = fmaf(a.w, b.w, -r.Ph);
     r.Dh = r.d * r.d;
     r.Dl = fmaf(r.d, r.d, -r.Dh);
+    r.c2 = fmaf(a.w, b.w, -r.Dh) - r.Dl;
     return r;
-}
-
-__device__ __forceinline__ float cross2_32(const PairInts &r)
-{
-    // (Ph - Dh) is exact when the two are within a factor 2 (Sterbenz), and
-    // (Pl - Dl) is a difference of small exact integers; the result has one
-    // rounding, i.e. relative error <= u (<= 2u when the angle exceeds 45 deg).
-    return (r.Ph - r.Dh) + (r.Pl - r.Dl);
 }
 
 // Eq. (2) angle in FP32: theta = atan2(sqrt(c2), d) via t = min(tan, cot).
 // Relative error <= 16u (rsqrt 2 ulp, the Lagrange c2, the polynomial).
 __device__ __forceinline__ float angle32(const PairInts &r)
 {
-    const float c2 = cross2_32(r);
+    const float c2 = r.c2;
     // c2 * d^2 is 0 or >= 1 (integers), so adding 1e-30 only guards the zero
     const float m = fmaf(c2, r.Dh, 1e-30f);
     const float rs = rsqrtf(m);
@@ -255,7 +253,7 @@ __device__ __forceinline__ float minimax32(const PairInts &r, const Aux xa, cons
 {
     const float v = (4.0f * r.Dh - r.Ph) + (4.0f * r.Dl - r.Pl);
     const bool upper = (v >= 0.0f) && (r.Ph > 0.0f);
-    const float c2 = cross2_32(r);
+    const float c2 = r.c2;
     const float np = xa.a * xb.a;                              // |x||y|
     const float tau = c2 * rsqrtf(fmaxf(c2 * np * (np + r.d), 1e-30f));   // sqrt(1 - z)
     const float z = r.d * xa.b * xb.b;                         // 0 for a zero vector
