@@ -42,6 +42,21 @@ CONFIG = {"workload": WORKLOAD, "M": M, "N": N, "win": WIN, "filter": FILTER, "p
           "noise": NOISE, "rectangles": RECTS, "frames_in_rotation": FRAMES,
           "l2": "inputs larger than L2: 24 distinct frames (149 MB) in rotation"}
 
+
+
+def use_4k_workload():
+    """The precision stress case (3840 x 2160, 20% impulsive noise): same
+    filter and path, frames rebound for every function of this module."""
+    global M, N, NOISE, FRAMES, WORKLOAD, METRIC, CONFIG
+    M, N, NOISE, FRAMES = 2160, 3840, 0.20, 6
+    WORKLOAD = ("DDF 5x5 (p=0.25, exact arccos) on 3840x2160 RGB uint8: sinusoid field + 12 flat rectangles, "
+                "20% impulsive noise")
+    METRIC = "Mpix/s, 5x5 DDF on 4K RGB, 20% noise: FP32+FP64-tie path vs plain FP64 GPU path"
+    CONFIG = {"workload": WORKLOAD, "M": M, "N": N, "win": WIN, "filter": FILTER, "p": P, "dist": DIST,
+              "noise": NOISE, "rectangles": RECTS, "frames_in_rotation": FRAMES,
+              "l2": "inputs larger than L2: 6 distinct frames (149 MB) in rotation"}
+
+
 # FP32-pipe lane operations per output pixel of the FP32 tile kernel for this
 # workload, counted from the source (see the design notes): 40 unique pair
 # terms x 30 ops, separable window sums 2 x 305 adds, 25 DDF scores x 15 ops
@@ -174,7 +189,7 @@ def cpu_oracle_rate(seconds_target: float = 12.0, sample_pixels: int | None = No
     oracle.filter_u8(img, WIN, FILTER, P, DIST, Q, pixels=pix)
     dt = time.perf_counter() - t0
     return {"value": n / dt / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{n} random pixels of one 1920x1080 frame ({dt:.1f} s of CPU work, all cores)"}
+            "sample": f"{n} random pixels of one {N}x{M} frame ({dt:.1f} s of CPU work, all cores)"}
 
 
 def run_reference(args):
@@ -204,7 +219,7 @@ def run_reference(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": CONFIG,
             "impl": "reference",
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"{per_step} random pixels of one 1920x1080 frame per step"},
+                             "sample": f"{per_step} random pixels of one {N}x{M} frame per step"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -281,10 +296,12 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=None)
-    ap.add_argument("--workload", default="ddf5_1080p", choices=["ddf5_1080p", "batch"])
+    ap.add_argument("--workload", default="ddf5_1080p", choices=["ddf5_1080p", "ddf5_4k", "batch"])
     ap.add_argument("--shape", type=int, default=None, help="force this FP32 tile shape instead of autotuning")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.workload == "ddf5_4k":
+        use_4k_workload()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batch":
@@ -311,8 +328,8 @@ def main():
     outs = [torch.empty_like(x) for x in ins]
     idxs = [torch.empty((M, N), dtype=torch.int8, device=dev) for _ in ins]
     wsb = vdf.workspace_bytes(M, N, "fp32")
-    # two workspaces: the FP64 recheck of frame i (second stream) overlaps the
-    # FP32 pass of frame i+1
+    # three workspaces: the FP64 recheck of frame i (second stream) overlaps
+    # the FP32 passes of frames i+1 and i+2
     wst = [torch.empty(wsb + 256, dtype=torch.uint8, device=dev) for _ in range(3)]
     wsp = [vdf._aligned(w) for w in wst]
     side = torch.cuda.Stream(dev)

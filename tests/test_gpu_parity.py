@@ -151,6 +151,23 @@ def test_full_size_1080p_sampled(V, O, filter, p, win):
     assert ov == 0
 
 
+def test_full_size_4k_20pct_noise(V, O):
+    """The precision stress case: DDF 5x5 (p = 0.25) on 3840 x 2160 with 20%
+    impulsive noise.  The FP32 path with its FP64 recheck equals the plain
+    FP64 path on every pixel, and the oracle on 4000 sampled pixels."""
+    from paper_1009_0958_gb300 import synth
+    _, img = synth.make_image(2160, 3840, 11, 0.20, rectangles=12)
+    out, idx, _, (rc, ov) = run(V, img, 5, "ddf", 0.25, "exact", 4, "fp32")
+    out64, idx64, _, _ = run(V, img, 5, "ddf", 0.25, "exact", 4, "fp64")
+    assert ov == 0 and rc > 0
+    assert np.array_equal(idx, idx64) and np.array_equal(out, out64)
+    rng = np.random.default_rng(2)
+    pix = np.concatenate([rng.integers(0, 2160 * 3840, 3990), [0, 3839, 2160 * 3840 - 1, 2159 * 3840]])
+    ref = O.filter_u8(img, 5, "ddf", 0.25, "exact", 4, pixels=pix)
+    assert np.array_equal(idx.reshape(-1)[pix], ref["idx"])
+    assert np.array_equal(out.reshape(-1, 3)[pix], ref["out"])
+
+
 @pytest.mark.parametrize("win", [3, 5])
 @pytest.mark.parametrize("filter,p", [("bvdf", 0.5), ("ddf", 0.25), ("ddf", 0.5), ("ddf", 0.3), ("ddf", 1.0)])
 @pytest.mark.parametrize("dist,q", [("exact", 4), ("minimax", 4), ("minimax", 3), ("rgb", 4)])
