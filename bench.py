@@ -66,7 +66,7 @@ SMS, FP32_LANES_PER_SM = 152, 128
 
 # DRAM bytes per launch of the FP32 tile kernel, from one ncu capture, keyed
 # by a hash of the kernel sources it was taken on (null once they change).
-TRAFFIC_BY_SOURCE = {"89ba1f4833938470": 6299392}   # profiles/tile_kernel_fp32_ddf5_1080p.md
+TRAFFIC_BY_SOURCE = {"30099f8f46c612c4": 6296064}   # profiles/tile_kernel_fp32_ddf5_1080p.md
 
 
 def kernel_source_hash() -> str:
@@ -288,6 +288,57 @@ def run_batch_workload(args):
     print(json.dumps(line), flush=True)
 
 
+def run_autograd_workload(args):
+    """The differentiable workload: DDF 3x3 (p = 0.25) forward on a float32
+    32 x 3 x 512 x 512 batch in [0, 1] (FP64 kernels on float input) plus the
+    gather-form backward; the backward kernel is HBM-bound at 25 B/px."""
+    import torch
+
+    from paper_1009_0958_gb300 import build as vbuild
+    from paper_1009_0958_gb300 import synth, vdf
+    vbuild.build()
+    dev = torch.device("cuda", 0)
+    B, Mf, Nf = 32, 512, 512
+    field = np.stack([synth.make_image(Mf, Nf, 300 + b, NOISE)[1] for b in range(B)])
+    x = torch.from_numpy(synth.to_float_nchw(field)).to(dev)
+    gy = torch.randn_like(x)
+    y, idx, gx = torch.empty_like(x), torch.empty((B, Mf, Nf), dtype=torch.int8, device=dev), torch.empty_like(x)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        vdf.filter_f32(x, 3, "ddf", P, precision="fp64", out=y, index=idx)
+        vdf.backward_f32(gy, idx, 3, grad_x=gx)
+    for _ in range(args.warmup):
+        step()
+    K = max(3, min(args.steps, 20))
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
+    torch.cuda.synchronize(dev)
+    with ClockSampler(0) as clk:
+        for k in range(K):
+            ev[k][0].record(stream)
+            vdf.filter_f32(x, 3, "ddf", P, precision="fp64", out=y, index=idx)
+            ev[k][1].record(stream)
+            vdf.backward_f32(gy, idx, 3, grad_x=gx)
+            ev[k][2].record(stream)
+        torch.cuda.synchronize(dev)
+    fwd = statistics.mean(a.elapsed_time(b) for a, b, _ in ev)
+    bwd = statistics.mean(b.elapsed_time(c) for _, b, c in ev)
+    px = B * Mf * Nf
+    bw = 25.0 * px / (bwd * 1e-3) / 1e9   # grad_y 12 B + index 1 B + grad_x 12 B per pixel
+    line = {"metric": "Mpix/s, DDF 3x3 forward + backward on float32 32x3x512x512 (differentiable path)",
+            "value": px / ((fwd + bwd) * 1e-3) / 1e6, "unit": UNIT, "n_gpus": 1, "steps": K,
+            "warmup": args.warmup, "ms_per_step": fwd + bwd, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64 forward, f32 backward", "data": "synthetic",
+            "config": {"workload": "32 x 3 x 512 x 512 float32 in [0, 1]: sinusoid field / 255 + 10% impulses, "
+                                   "DDF 3x3, p = 0.25, exact arccos"},
+            "forward_ms": fwd, "backward_ms": bwd,
+            "roofline": {"bound": "hbm", "kernel": "vdf::backward_gather<R=1>", "achieved": bw,
+                         "peak": 6793.1, "unit": "GB/s", "frac": bw / 6793.1, "traffic": None,
+                         "algorithmic_bytes_per_pixel": 25},
+            "gpu_launches": 2 * K, "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -296,7 +347,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=None)
-    ap.add_argument("--workload", default="ddf5_1080p", choices=["ddf5_1080p", "ddf5_4k", "batch"])
+    ap.add_argument("--workload", default="ddf5_1080p", choices=["ddf5_1080p", "ddf5_4k", "batch", "autograd"])
     ap.add_argument("--shape", type=int, default=None, help="force this FP32 tile shape instead of autotuning")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -306,6 +357,8 @@ def main():
         return run_reference(args)
     if args.workload == "batch":
         return run_batch_workload(args)
+    if args.workload == "autograd":
+        return run_autograd_workload(args)
 
     import torch
     import torch.distributed as dist
