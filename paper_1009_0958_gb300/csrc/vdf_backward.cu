@@ -12,58 +12,179 @@
 // (including at the borders, where clamping only moves sources inward), so
 // each thread gathers over the (2R+1)^2 neighbourhood of its own q in a fixed
 // order: no atomics, bit-reproducible.
+#include <type_traits>
+
 #include "vdf_dispatch.h"
 
 namespace vdf {
 
 namespace {
 
-template <int R>
+// A block gathers a kTX x kTY tile: the gradients and indices of the tile
+// and a ring around it are first staged in shared memory (entries outside
+// the image get index -1), then each thread gathers for kQ pixels of one row
+// from there.  For each q the sources are added in raster order of p.  A
+// thread whose sources all lie at least R pixels inside the image tests a
+// source with one compare (p selects q exactly when its member offset is
+// q - p); threads near the border apply the clamped test.
+//
+// Staging: with VEC (N a multiple of 4, 16-byte aligned gradients) rows are
+// read as float4 / 32-bit words over columns bx - 4 .. bx + kTX + 3 (every
+// vector is inside the image or wholly outside it); otherwise element by
+// element over bx - R .. bx + kTX + R - 1.
+constexpr int kTX = 128, kTY = 8, kQ = 4;
+
+template <int R, bool VEC>
 __global__ void __launch_bounds__(256) backward_gather(const float *__restrict__ gy, const int8_t *__restrict__ idx,
                                                        float *__restrict__ gx, int M, int N)
 {
-    constexpr int W = 2 * R + 1;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y;
-    const int b = blockIdx.z;
-    if (x >= N) return;
+    constexpr int W = 2 * R + 1, HY = kTY + 2 * R;
+    constexpr int C0 = VEC ? 4 : R;            // staged column of image column bx
+    constexpr int HX = kTX + 2 * C0;
+    __shared__ __align__(16) float sg[3][HY][HX];
+    __shared__ __align__(16) int8_t si[HY][HX];
+    const int bx = blockIdx.x * kTX, by = blockIdx.y * kTY, b = blockIdx.z;
     const size_t plane = (size_t)M * N;
     const int8_t *ib = idx + (size_t)b * plane;
     const float *g = gy + (size_t)b * 3 * plane;
-    float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+    const int tid = threadIdx.x;
+    if constexpr (VEC) {
+        // HY rows x HX / 4 vectors; each thread issues all its loads first
+        constexpr int NV = HY * (HX / 4), PER = (NV + 255) / 256;
+        float4 v[3][PER];
+        int w[PER];
 #pragma unroll
-    for (int dy = -R; dy <= R; ++dy) {
-        const int py = y + dy;
-        if (py < 0 || py >= M) continue;
+        for (int k = 0; k < PER; ++k) {
+            const int e = tid + 256 * k;
+            const int r = e / (HX / 4), c4 = e - r * (HX / 4);
+            const int py = by - R + r, px = bx - C0 + 4 * c4;
+            const bool in = e < NV && py >= 0 && py < M && px >= 0 && px < N;
+            const size_t o = in ? (size_t)py * N + px : 0;
+            w[k] = in ? __ldg(reinterpret_cast<const int *>(ib + o)) : -1;
 #pragma unroll
-        for (int dx = -R; dx <= R; ++dx) {
-            const int px = x + dx;
-            if (px < 0 || px >= N) continue;
-            const size_t o = (size_t)py * N + px;
-            const int i = ib[o];
-            const int sy = min(max(py + i / W - R, 0), M - 1);
-            const int sx = min(max(px + i % W - R, 0), N - 1);
-            if (sy == y && sx == x) {
-                a0 += g[o];
-                a1 += g[plane + o];
-                a2 += g[2 * plane + o];
-            }
+            for (int c = 0; c < 3; ++c)
+                v[c][k] = in ? __ldg(reinterpret_cast<const float4 *>(g + c * plane + o)) : make_float4(0, 0, 0, 0);
+        }
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            const int e = tid + 256 * k;
+            if (e >= NV) continue;
+            const int r = e / (HX / 4), c4 = e - r * (HX / 4);
+            *reinterpret_cast<int *>(&si[r][4 * c4]) = w[k];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) *reinterpret_cast<float4 *>(&sg[c][r][4 * c4]) = v[c][k];
+        }
+    } else {
+        constexpr int PER = (HY * HX + 255) / 256;
+        float v0[PER], v1[PER], v2[PER];
+        int vi[PER];
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            const int e = tid + 256 * k;
+            const int r = e / HX, c = e - r * HX;
+            const int py = by - R + r, px = bx - C0 + c;
+            const bool in = e < HY * HX && py >= 0 && py < M && px >= 0 && px < N;
+            const size_t o = in ? (size_t)py * N + px : 0;
+            vi[k] = in ? (int)__ldg(ib + o) : -1;
+            v0[k] = in ? __ldg(g + o) : 0.0f;
+            v1[k] = in ? __ldg(g + plane + o) : 0.0f;
+            v2[k] = in ? __ldg(g + 2 * plane + o) : 0.0f;
+        }
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            const int e = tid + 256 * k;
+            if (e >= HY * HX) continue;
+            const int r = e / HX, c = e - r * HX;
+            si[r][c] = (int8_t)vi[k];
+            sg[0][r][c] = v0[k];
+            sg[1][r][c] = v1[k];
+            sg[2][r][c] = v2[k];
         }
     }
-    float *o = gx + (size_t)b * 3 * plane + (size_t)y * N + x;
-    o[0] = a0;
-    o[plane] = a1;
-    o[2 * plane] = a2;
+    __syncthreads();
+    const int ty = tid / (kTX / kQ), x0 = (tid % (kTX / kQ)) * kQ;   // tile coordinates
+    const int y = by + ty, X0 = bx + x0;
+    if (y >= M || X0 >= N) return;
+    // the index bytes of the thread's neighbourhood: VEC reads the three
+    // words at staged columns x0, x0 + 4, x0 + 8 of each row (columns
+    // x0 + 4 - R .. x0 + 7 + R are needed), otherwise byte by byte
+    unsigned iw[W][3];
+    if constexpr (VEC) {
+#pragma unroll
+        for (int r = 0; r < W; ++r)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) iw[r][k] = *reinterpret_cast<const unsigned *>(&si[ty + r][x0 + 4 * k]);
+    }
+    auto member = [&](int r, int c) -> int {   // r = row in the neighbourhood, c = staged column
+        if constexpr (VEC) {
+            const int k = c - x0;                  // 0 .. 11, known at compile time after unrolling
+            return (int)(int8_t)(iw[r][k >> 2] >> (8 * (k & 3)));
+        } else {
+            return si[ty + r][c];
+        }
+    };
+    float acc[3][kQ];
+    auto gather = [&](auto fast) {
+#pragma unroll
+        for (int j = 0; j < kQ; ++j) {
+            acc[0][j] = acc[1][j] = acc[2][j] = 0.0f;
+#pragma unroll
+            for (int dy = -R; dy <= R; ++dy)
+#pragma unroll
+                for (int dx = -R; dx <= R; ++dx) {
+                    const int r = ty + R + dy, c = x0 + j + C0 + dx;
+                    const int i = member(R + dy, c);
+                    bool hit;
+                    if constexpr (decltype(fast)::value) {
+                        hit = i == (R - dy) * W + (R - dx);
+                    } else {
+                        const int sy = min(max(y + dy + i / W - R, 0), M - 1);
+                        const int sx = min(max(X0 + j + dx + i % W - R, 0), N - 1);
+                        hit = i >= 0 && sy == y && sx == X0 + j;
+                    }
+                    if (hit) {
+                        acc[0][j] += sg[0][r][c];
+                        acc[1][j] += sg[1][r][c];
+                        acc[2][j] += sg[2][r][c];
+                    }
+                }
+        }
+    };
+    // the branch is taken once per thread, outside the unrolled loops
+    if (y >= 2 * R && y < M - 2 * R && X0 >= 2 * R && X0 + kQ - 1 + 2 * R < N)
+        gather(std::true_type{});
+    else
+        gather(std::false_type{});
+    float *o = gx + (size_t)b * 3 * plane + (size_t)y * N + X0;
+    if (VEC && X0 + kQ <= N) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            *reinterpret_cast<float4 *>(o + c * plane) = make_float4(acc[c][0], acc[c][1], acc[c][2], acc[c][3]);
+    } else {
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int j = 0; j < kQ; ++j)
+                if (X0 + j < N) o[c * plane + j] = acc[c][j];
+    }
 }
 
 }  // namespace
 
 cudaError_t run_backward(const float *gy, const int8_t *idx, float *gx, int B, int M, int N, int R, cudaStream_t st)
 {
-    dim3 block(256), grid((N + 255) / 256, M, B);
-    if (R == 1) backward_gather<1><<<grid, block, 0, st>>>(gy, idx, gx, M, N);
-    else if (R == 2) backward_gather<2><<<grid, block, 0, st>>>(gy, idx, gx, M, N);
-    else return cudaErrorInvalidValue;
+    // vectors when every row starts on a 16-byte (4-byte for the indices) boundary
+    const bool vec = N % 4 == 0 && ((uintptr_t)gy & 15) == 0 && ((uintptr_t)gx & 15) == 0 && ((uintptr_t)idx & 3) == 0;
+    dim3 block(256), grid((N + kTX - 1) / kTX, (M + kTY - 1) / kTY, B);
+    if (R == 1) {
+        if (vec) backward_gather<1, true><<<grid, block, 0, st>>>(gy, idx, gx, M, N);
+        else backward_gather<1, false><<<grid, block, 0, st>>>(gy, idx, gx, M, N);
+    } else if (R == 2) {
+        if (vec) backward_gather<2, true><<<grid, block, 0, st>>>(gy, idx, gx, M, N);
+        else backward_gather<2, false><<<grid, block, 0, st>>>(gy, idx, gx, M, N);
+    } else {
+        return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 
