@@ -62,6 +62,19 @@ def use_4k_workload():
 # terms x 30 ops, separable window sums 2 x 305 adds, 25 DDF scores x 15 ops
 # (log2 range reduction, combine, bound), selection 25 x 6 ops.
 ALU_OPS_PER_PIXEL = 40 * 30 + 2 * 305 + 25 * 15 + 25 * 6
+
+
+def ops_per_pixel(win: int, filt: str) -> int:
+    """The same source-level count for any window and filter: U = ((2w-1)^2-1)/2
+    pair terms of 30 ops (DDF: angle + L2) or 24 (BVDF: angle); per
+    aggregate component (2 for DDF) (2w-1) w (w-1) row-sum adds plus w^3
+    accumulator adds; per member 15 score ops (DDF) or 2 (BVDF) and 6
+    selection ops.  ops_per_pixel(5, "ddf") == ALU_OPS_PER_PIXEL."""
+    U, n = ((2 * win - 1) ** 2 - 1) // 2, win * win
+    sums = (2 * win - 1) * win * (win - 1) + win ** 3
+    if filt == "ddf":
+        return U * 30 + 2 * sums + n * 15 + n * 6
+    return U * 24 + sums + n * 2 + n * 6
 SMS, FP32_LANES_PER_SM = 152, 128
 
 # DRAM bytes per launch of the FP32 tile kernel, from one ncu capture, keyed
@@ -275,6 +288,13 @@ def run_batch_workload(args):
         torch.cuda.synchronize(dev)
     ms = e0.elapsed_time(e1) / K
     rechecked, overflow = plan.stats()
+    ops = sum(ops_per_pixel(w, f) * int(x.shape[0]) * int(x.shape[1]) for x, (w, f) in zip(imgs, cfgs))
+    achieved = ops / (ms * 1e-3) / 1e12
+    peak = SMS * FP32_LANES_PER_SM * 2.070e9 / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "T FP32-pipe ops/s",
+                "frac": achieved / peak, "traffic": None,
+                "kernel": "vdf::batch_kernel (the step's time, which also holds the batch recheck kernel)",
+                "ops_per_step": ops, "peak_basis": "152 SMs x 128 FP32 lanes x 2070 MHz max SM clock"}
     line = {"metric": "Mpix/s, batch of 256 uneven RGB images, mixed 3x3/5x5 BVDF/DDF, FP32+FP64-tie path",
             "value": pixels / (ms * 1e-3) / 1e6, "unit": UNIT, "n_gpus": 1, "steps": K, "warmup": args.warmup,
             "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -284,7 +304,7 @@ def run_batch_workload(args):
                        "pixels": pixels, "launch": "one persistent tile kernel + one recheck kernel per step, "
                                                    "replayed from a CUDA graph", "tuned_shapes": tuned},
             "recheck_fraction": rechecked / pixels, "overflow": overflow, "gpu_launches": 2 * K,
-            "clocks": clk.summary()}
+            "roofline": roofline, "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
 
 

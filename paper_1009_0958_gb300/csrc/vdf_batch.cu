@@ -71,10 +71,13 @@ constexpr int max_threads(std::integer_sequence<int, I...>)
 constexpr size_t kBatchSmem = max_smem(std::make_integer_sequence<int, kNumCfgs>{});
 constexpr int kBatchThreads = max_threads(std::make_integer_sequence<int, kNumCfgs>{});
 
+// One configuration's tile body as a call of its own: each body gets its own
+// register allocation instead of the union of all twelve.
 template <int CFG>
-__device__ __forceinline__ void run_item(const TileParams &prm, int t, int tiles_x, unsigned char *smem)
+__device__ __noinline__ void run_item(const TileParams prm, int t, int tiles_x)
 {
     using C = typename BCfg<CFG>::C;
+    extern __shared__ __align__(16) unsigned char smem[];
     tile_body<C, kBatchThreads>(prm, 0, (t % tiles_x) * C::TW, (t / tiles_x) * C::TH, smem);
 }
 
@@ -82,7 +85,7 @@ template <int... I>
 __device__ __forceinline__ void dispatch_item(int cfg, const TileParams &prm, int t, int tiles_x, unsigned char *smem,
                                               std::integer_sequence<int, I...>)
 {
-    ((cfg == I ? run_item<I>(prm, t, tiles_x, smem) : void()), ...);
+    ((cfg == I ? run_item<I>(prm, t, tiles_x) : void()), ...);
 }
 
 __global__ void __launch_bounds__(kBatchThreads, 1) batch_kernel(const BatchParams bp)
