@@ -89,9 +89,9 @@ struct TileCfg {
     static constexpr size_t SMEM = PIX_BYTES + AUX_BYTES + KEY_BYTES + UNION_BYTES;
     static_assert(FP64 || PIX_BYTES >= sizeof(PlaneT) * (2 * R * CW + 2 * R), "FP32 plane reads stay in the block");
     // CTAs per SM the register budget is sized for: two when two fit in the
-    // SM's 228 KB of shared memory (1 KB reserved per CTA) with at least 64
+    // SM's 228 KB of shared memory (1 KB reserved per CTA) with at least 48
     // registers per thread, so one CTA's barrier waits overlap the other's work
-    static constexpr int MINB = (2 * (SMEM + 1024) <= 228 * 1024 && 2 * NT * 64 <= 65536) ? 2 : 1;
+    static constexpr int MINB = (2 * (SMEM + 1024) <= 228 * 1024 && 2 * NT * 48 <= 65536) ? 2 : 1;
 };
 
 // ------------------------------------------------------------ scores ------
