@@ -310,8 +310,9 @@ def run_batch_workload(args):
 
 def run_autograd_workload(args):
     """The differentiable workload: DDF 3x3 (p = 0.25) forward on a float32
-    32 x 3 x 512 x 512 batch in [0, 1] (FP64 kernels on float input) plus the
-    gather-form backward; the backward kernel is HBM-bound at 25 B/px."""
+    32 x 3 x 512 x 512 batch in [0, 1] (the FP32 certified path for float
+    input, with its FP64 recheck) plus the gather-form backward; the backward
+    kernel is HBM-bound at 25 B/px.  The plain FP64 forward is timed beside."""
     import torch
 
     from paper_1009_0958_gb300 import build as vbuild
@@ -325,8 +326,10 @@ def run_autograd_workload(args):
     y, idx, gx = torch.empty_like(x), torch.empty((B, Mf, Nf), dtype=torch.int8, device=dev), torch.empty_like(x)
     stream = torch.cuda.current_stream(dev)
 
+    ws = vdf.alloc_workspace(B * Mf, Nf, "fp32", dev)
+
     def step():
-        vdf.filter_f32(x, 3, "ddf", P, precision="fp64", out=y, index=idx)
+        vdf.filter_f32(x, 3, "ddf", P, precision="fp32", out=y, index=idx, workspace=ws)
         vdf.backward_f32(gy, idx, 3, grad_x=gx)
     for _ in range(args.warmup):
         step()
@@ -336,22 +339,32 @@ def run_autograd_workload(args):
     with ClockSampler(0) as clk:
         for k in range(K):
             ev[k][0].record(stream)
-            vdf.filter_f32(x, 3, "ddf", P, precision="fp64", out=y, index=idx)
+            vdf.filter_f32(x, 3, "ddf", P, precision="fp32", out=y, index=idx, workspace=ws)
             ev[k][1].record(stream)
             vdf.backward_f32(gy, idx, 3, grad_x=gx)
             ev[k][2].record(stream)
         torch.cuda.synchronize(dev)
     fwd = statistics.mean(a.elapsed_time(b) for a, b, _ in ev)
     bwd = statistics.mean(b.elapsed_time(c) for _, b, c in ev)
+    rechecked = vdf.workspace_stats(ws)[0]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    vdf.filter_f32(x, 3, "ddf", P, precision="fp64", out=y, index=idx)
+    e0.record(stream)
+    for _ in range(3):
+        vdf.filter_f32(x, 3, "ddf", P, precision="fp64", out=y, index=idx)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    fwd64 = e0.elapsed_time(e1) / 3
     px = B * Mf * Nf
     bw = 25.0 * px / (bwd * 1e-3) / 1e9   # grad_y 12 B + index 1 B + grad_x 12 B per pixel
     line = {"metric": "Mpix/s, DDF 3x3 forward + backward on float32 32x3x512x512 (differentiable path)",
             "value": px / ((fwd + bwd) * 1e-3) / 1e6, "unit": UNIT, "n_gpus": 1, "steps": K,
             "warmup": args.warmup, "ms_per_step": fwd + bwd, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64 forward, f32 backward", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f32+f64 forward, f32 backward", "data": "synthetic",
             "config": {"workload": "32 x 3 x 512 x 512 float32 in [0, 1]: sinusoid field / 255 + 10% impulses, "
                                    "DDF 3x3, p = 0.25, exact arccos"},
-            "forward_ms": fwd, "backward_ms": bwd,
+            "forward_ms": fwd, "backward_ms": bwd, "forward_fp64_ms": fwd64,
+            "forward_recheck_fraction": rechecked / px,
             "roofline": {"bound": "hbm", "kernel": "vdf::backward_gather<R=1>", "achieved": bw,
                          "peak": 6793.1, "unit": "GB/s", "frac": bw / 6793.1, "traffic": None,
                          "algorithmic_bytes_per_pixel": 25},

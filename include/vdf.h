@@ -164,8 +164,13 @@ int vdf_filter_host_frames(const uint8_t *const *img_host, uint8_t *const *out_h
  * shape; index_out: device, B x M x N int8 (may be NULL, but the backward
  * pass needs it).  Only VDF_DIST_EXACT is supported for float input.  The
  * FP64 precision computes the pair terms from the float32 values exactly
- * promoted to double; VDF_PREC_FP32_RECHECK needs workspace of
- * vdf_workspace_bytes(B * M, N, precision) bytes.  Errors as vdf_filter.
+ * promoted to double.  VDF_PREC_FP32_RECHECK computes them in FP32 on
+ * exponent-normalised pixels with certified bounds (Kahan cross products)
+ * and rechecks in FP64 the pixels the bounds leave open, the windows with an
+ * aggregate below 2^-23, and every tile holding a negative, non-finite,
+ * subnormal or extreme component; it selects what the FP64 precision
+ * selects.  It needs workspace of vdf_workspace_bytes(B * M, N, precision)
+ * bytes (256-byte aligned).  Errors as vdf_filter.
  */
 int vdf_filter_f32(const float *img, int B, int M, int N, int win, int filter, double p, int dist_mode,
                    int minimax_q, int precision, float *out, int8_t *index_out, void *workspace,
@@ -295,6 +300,27 @@ int vdf_debug_fp32_scores(const uint8_t *img, int M, int N, int win, int filter,
  */
 int vdf_debug_fp32_terms(const int *pairs, int n, int dist_mode, int minimax_q, float *angle_out, float *l2_out,
                          void *stream);
+
+/*
+ * Diagnostic: the FP32 exact-mode terms of n pairs of float pixels as the
+ * float32-input FP32 tile kernel computes them (exponent-normalised pixels,
+ * Kahan cross products; Eq. (2) and |x - y|).  pairs: device, n x 6 floats
+ * (x then y, raw values); angle_out, l2_out: device, n floats each, or NULL;
+ * NaN for a pair with an unsafe pixel (see vdf_filter_f32).  Bounds the path
+ * relies on: angle relative 24u, L2 relative 8u, plus absolute 2^-58 and
+ * 2^-62 where a product underflows.  The paper has no such call.
+ * Errors: VDF_E_INVALID for null pairs or n < 0.
+ */
+int vdf_debug_fp32_terms_f32(const float *pairs, int n, float *angle_out, float *l2_out, void *stream);
+
+/*
+ * Diagnostic: the largest relative error, in units of u = 2^-24, of the
+ * approximate square root the FP32 L2 terms use, over every positive normal
+ * float (about 2.1e9 evaluations).  max_rel_err_u: device, one float,
+ * written asynchronously on stream.  The paper has no such call.
+ * Errors: VDF_E_INVALID for a null pointer.
+ */
+int vdf_debug_sqrt_error(float *max_rel_err_u, void *stream);
 
 #ifdef __cplusplus
 }

@@ -34,6 +34,7 @@ UNIT_FLAGS = {
     "vdf_fp32_s3.cu": ["-ftz=true"],
     "vdf_batch.cu": ["-ftz=true"],
     "vdf_debug.cu": ["-ftz=true"],
+    "vdf_fp32f.cu": ["-ftz=true"],
 }
 
 

@@ -248,7 +248,8 @@ int vdf_filter_f32(const float *img, int B, int M, int N, int win, int filter, d
     const size_t bytes = (size_t)B * M * N * 3 * sizeof(float);
     if (overlaps(img, bytes, out, bytes)) return VDF_E_INVALID;
     if (dist_mode != VDF_DIST_EXACT) return VDF_E_UNSUPPORTED;
-    if (precision != VDF_PREC_FP64) return VDF_E_UNSUPPORTED;
+    if (index_out && (overlaps(index_out, (size_t)B * M * N, img, bytes) || overlaps(index_out, (size_t)B * M * N, out, bytes)))
+        return VDF_E_INVALID;
     vdf::TileParams prm{};
     prm.img = img;
     prm.out = out;
@@ -258,7 +259,32 @@ int vdf_filter_f32(const float *img, int B, int M, int N, int win, int filter, d
     prm.B = B;
     prm.p = p;
     prm.q = minimax_q;
-    return cuda_fail(vdf::run_fp64(prm, win / 2, filter, dist_mode, true, (cudaStream_t)stream));
+    cudaStream_t st = (cudaStream_t)stream;
+    if (precision == VDF_PREC_FP64) return cuda_fail(vdf::run_fp64(prm, win / 2, filter, dist_mode, true, st));
+    // FP32 certified pass over the batch, then the FP64 recheck of the listed
+    // pixels (batch pixel ids); the workspace is sized for B * M rows of N
+    const size_t need = vdf_workspace_bytes(B * M, N, precision);
+    if (!workspace || workspace_bytes < need || ((uintptr_t)workspace & 255)) return VDF_E_WORKSPACE;
+    prm.recheck_ctr = (unsigned *)workspace;
+    prm.recheck_list = (int2 *)((char *)workspace + kCtrBytes);
+    prm.recheck_cap = (unsigned)((size_t)B * M * N);
+    cudaError_t e = cudaMemsetAsync(prm.recheck_ctr, 0, 2 * sizeof(unsigned), st);
+    if (e == cudaSuccess) e = vdf::run_fp32_f32in(prm, win / 2, filter, st);
+    if (e == cudaSuccess) {
+        vdf::RecheckParams rp{};
+        rp.img = img;
+        rp.out = out;
+        rp.idx = index_out;
+        rp.list = prm.recheck_list;
+        rp.ctr = prm.recheck_ctr;
+        rp.cap = prm.recheck_cap;
+        rp.M = M;
+        rp.N = N;
+        rp.p = p;
+        rp.q = minimax_q;
+        e = vdf::run_recheck(rp, win / 2, filter, dist_mode, num_sms() * 4, st, true);
+    }
+    return cuda_fail(e);
 }
 
 int vdf_backward_f32(const float *grad_y, const int8_t *index, int B, int M, int N, int win, float *grad_x,
@@ -369,6 +395,18 @@ int vdf_debug_fp32_terms(const int *pairs, int n, int dist_mode, int minimax_q, 
     if (!pairs || n < 0 || dist_mode < VDF_DIST_EXACT || dist_mode > VDF_DIST_RGB) return VDF_E_INVALID;
     if (dist_mode == VDF_DIST_MINIMAX && (minimax_q < 2 || minimax_q > 4)) return VDF_E_INVALID;
     return cuda_fail(vdf::run_debug_terms(pairs, n, dist_mode, minimax_q, angle_out, l2_out, (cudaStream_t)stream));
+}
+
+int vdf_debug_fp32_terms_f32(const float *pairs, int n, float *angle_out, float *l2_out, void *stream)
+{
+    if (!pairs || n < 0) return VDF_E_INVALID;
+    return cuda_fail(vdf::run_debug_terms_f32(pairs, n, angle_out, l2_out, (cudaStream_t)stream));
+}
+
+int vdf_debug_sqrt_error(float *max_rel_err_u, void *stream)
+{
+    if (!max_rel_err_u) return VDF_E_INVALID;
+    return cuda_fail(vdf::run_debug_sqrt_error(reinterpret_cast<unsigned *>(max_rel_err_u), (cudaStream_t)stream));
 }
 
 }  // extern "C"

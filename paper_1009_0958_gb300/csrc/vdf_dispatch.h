@@ -21,11 +21,19 @@ inline constexpr TileShape kShapes32[kNumShapes32] = {{32, 16}, {32, 8}, {16, 16
 cudaError_t run_fp32(const TileParams &prm, int R, int filter, int dist, int shape, cudaStream_t st);
 // Gradient gather of the float32 path.
 cudaError_t run_backward(const float *gy, const int8_t *idx, float *gx, int B, int M, int N, int R, cudaStream_t st);
-// FP64 recheck of the pixels listed by run_fp32.
-cudaError_t run_recheck(const RecheckParams &prm, int R, int filter, int dist, int blocks, cudaStream_t st);
+// FP32 certified tile kernel for float32 B x 3 x M x N input (exact mode, 32x16 tiles).
+cudaError_t run_fp32_f32in(const TileParams &prm, int R, int filter, cudaStream_t st);
+// FP64 recheck of the pixels listed by run_fp32 (f32in: by run_fp32_f32in).
+cudaError_t run_recheck(const RecheckParams &prm, int R, int filter, int dist, int blocks, cudaStream_t st,
+                        bool f32in = false);
 
 // FP32 pair terms of n pixel pairs (n x 6 ints), as the FP32 tile kernel computes them.
 cudaError_t run_debug_terms(const int *pairs, int n, int dist, int q, float *angle_out, float *l2_out,
                             cudaStream_t st);
+// The same for float pixels (n x 6 floats; NaN where a pixel is unsafe).
+cudaError_t run_debug_terms_f32(const float *pairs, int n, float *angle_out, float *l2_out, cudaStream_t st);
+// Largest relative error (units of 2^-24, as float bits) of the approximate
+// square root over every positive normal float.
+cudaError_t run_debug_sqrt_error(unsigned *max_err_bits, cudaStream_t st);
 
 }  // namespace vdf

@@ -42,8 +42,12 @@ cudaError_t by_dist(const TileParams &prm, int dist, bool f32in, cudaStream_t st
 }
 
 template <int R, int FILTER>
-cudaError_t recheck_by_dist(const RecheckParams &prm, int dist, int blocks, cudaStream_t st)
+cudaError_t recheck_by_dist(const RecheckParams &prm, int dist, bool f32in, int blocks, cudaStream_t st)
 {
+    if (f32in) {
+        if (dist != EXACT) return cudaErrorInvalidValue;
+        return launch_recheck<R, FILTER, EXACT, true>(prm, blocks, st);
+    }
     switch (dist) {
     case EXACT: return launch_recheck<R, FILTER, EXACT>(prm, blocks, st);
     case MINIMAX: return launch_recheck<R, FILTER, MINIMAX>(prm, blocks, st);
@@ -61,14 +65,15 @@ cudaError_t run_fp64(const TileParams &prm, int R, int filter, int dist, bool f3
     return cudaErrorInvalidValue;
 }
 
-cudaError_t run_recheck(const RecheckParams &prm, int R, int filter, int dist, int blocks, cudaStream_t st)
+cudaError_t run_recheck(const RecheckParams &prm, int R, int filter, int dist, int blocks, cudaStream_t st,
+                        bool f32in)
 {
     if (R == 1)
-        return filter == DDF ? recheck_by_dist<1, DDF>(prm, dist, blocks, st)
-                             : recheck_by_dist<1, BVDF>(prm, dist, blocks, st);
+        return filter == DDF ? recheck_by_dist<1, DDF>(prm, dist, f32in, blocks, st)
+                             : recheck_by_dist<1, BVDF>(prm, dist, f32in, blocks, st);
     if (R == 2)
-        return filter == DDF ? recheck_by_dist<2, DDF>(prm, dist, blocks, st)
-                             : recheck_by_dist<2, BVDF>(prm, dist, blocks, st);
+        return filter == DDF ? recheck_by_dist<2, DDF>(prm, dist, f32in, blocks, st)
+                             : recheck_by_dist<2, BVDF>(prm, dist, f32in, blocks, st);
     return cudaErrorInvalidValue;
 }
 

@@ -203,16 +203,15 @@ __device__ __forceinline__ PairInts pair_ints(const float4 a, const float4 b)
     return r;
 }
 
-// Eq. (2) angle in FP32: theta = atan2(sqrt(c2), d) via t = min(tan, cot).
-// Relative error <= 16u (rsqrt 2 ulp, the Lagrange c2, the polynomial).
-__device__ __forceinline__ float angle32(const PairInts &r)
+// theta = atan2(sqrt(c2), d) from c2 = |x x y|^2 and Dh = d^2 via
+// t = min(tan, cot): one reciprocal square root of c2 d^2, whose zero is
+// guarded by adding `guard` (below every non-zero c2 d^2 that matters).
+__device__ __forceinline__ float angle_core(float c2, float Dh, float guard)
 {
-    const float c2 = r.c2;
-    // c2 * d^2 is 0 or >= 1 (integers), so adding 1e-30 only guards the zero
-    const float m = fmaf(c2, r.Dh, 1e-30f);
+    const float m = fmaf(c2, Dh, guard);
     const float rs = rsqrtf(m);
-    const float ta = c2 * rs;     // sqrt(c2)/d = tan(theta)
-    const float tb = r.Dh * rs;   // d/sqrt(c2) = cot(theta)
+    const float ta = c2 * rs;   // sqrt(c2)/d = tan(theta)
+    const float tb = Dh * rs;   // d/sqrt(c2) = cot(theta)
     const float t = fminf(ta, tb);
     const float s = t * t;
     float v = atan_q(7);
@@ -223,6 +222,14 @@ __device__ __forceinline__ float angle32(const PairInts &r)
     return (ta >= tb) ? (kHalfPi32 - a) : a;
 }
 
+// Eq. (2) angle in FP32: theta = atan2(sqrt(c2), d) via t = min(tan, cot).
+// Relative error <= 16u (rsqrt 2 ulp, the Lagrange c2, the polynomial).
+__device__ __forceinline__ float angle32(const PairInts &r)
+{
+    // c2 * d^2 is 0 or >= 1 (integers), so adding 1e-30 only guards the zero
+    return angle_core(r.c2, r.Dh, 1e-30f);
+}
+
 // |x - y| in FP32.  e = |x - y|^2 is an exact integer in [0, 3 * 255^2]; on
 // that domain the approximate square root (one SFU operation) is within 2u
 // of the exact value (1.67u at worst; every attainable input is checked on
@@ -231,6 +238,70 @@ __device__ __forceinline__ float angle32(const PairInts &r)
 __device__ __forceinline__ float l2term32(const float4 a, const float4 b, float d)
 {
     const float e = fmaf(-2.0f, d, a.w + b.w);
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(e));
+    return r;
+}
+
+// ------------------------------------------ FP32 terms, float32 input ----
+// A float pixel x >= 0 is held exponent-normalised: {x 2^-k, 2^k} with the
+// largest component of x 2^-k in [1, 2) (an exact scaling; a zero vector is
+// {0, 1}).  Angles are scale-free, and x = (x 2^-k) 2^k exactly, so the L2
+// term reads the original values back.  A pixel is "safe" when every
+// component is +0 or a positive normal float whose exponent lies within 60
+// of the largest one's, and the largest one's exponent lies in [-60, 60];
+// pixels that are not (a negative, infinite, NaN or subnormal component, an
+// extreme magnitude or spread) are left to the FP64 recheck.  The
+// classification reads the bits, so it does not depend on flush-to-zero.
+
+// Normalised pixel, and whether it is safe.
+__device__ __forceinline__ float4 normalize_f32(float x, float y, float z, bool &safe)
+{
+    const int xb = __float_as_int(x), yb = __float_as_int(y), zb = __float_as_int(z);
+    const int ex = (xb >> 23) & 0xff, ey = (yb >> 23) & 0xff, ez = (zb >> 23) & 0xff;
+    const int em = max(ex, max(ey, ez));   // biased exponent of the largest component (all >= 0)
+    auto ok = [em](int bits, int e) {      // +0, or a positive normal within 60 octaves of the largest
+        return bits == 0 || (bits > 0 && e >= 1 && e <= 254 && e >= em - 60);
+    };
+    safe = ok(xb, ex) && ok(yb, ey) && ok(zb, ez) && (em == 0 || (em >= 127 - 60 && em <= 127 + 60));
+    if (!safe || em == 0) return make_float4(0.0f, 0.0f, 0.0f, 1.0f);
+    const float down = __int_as_float((254 - em) << 23), up = __int_as_float(em << 23);   // 2^-(em-127), 2^(em-127)
+    return make_float4(x * down, y * down, z * down, up);
+}
+
+// a b - c d by Kahan's algorithm: relative error <= 2u with FMA (Jeannerod,
+// Louvet and Muller, Math. Comp. 82 (2013)), barring underflow.
+__device__ __forceinline__ float det2(float a, float b, float c, float d)
+{
+    const float w = c * d;
+    const float e = fmaf(-c, d, w);   // w - c d, exactly
+    const float f = fmaf(a, b, -w);
+    return f + e;
+}
+
+// Eq. (2) angle of two normalised safe pixels.  d (three non-negative
+// products, FMA chain): <= 3u; each cross component <= 2u (Kahan), so
+// |x x y|^2 <= 6u and d^2 <= 7u; the rest as angle32.  Relative error
+// <= 24u (doubled by the bound's safety factor), plus an absolute 2^-58
+// where a tiny product underflows; the guard 2^-120 lies below c2 d^2 except
+// for angles within 2^-58 of 0 or pi/2.
+__device__ __forceinline__ float angle32f(const float4 a, const float4 b)
+{
+    const float d = fmaf(a.z, b.z, fmaf(a.y, b.y, a.x * b.x));
+    const float c0 = det2(a.y, b.z, a.z, b.y), c1 = det2(a.z, b.x, a.x, b.z), c2 = det2(a.x, b.y, a.y, b.x);
+    const float cc = fmaf(c2, c2, fmaf(c1, c1, c0 * c0));
+    return angle_core(cc, d * d, 0x1p-120f);
+}
+
+// |x - y| of two normalised safe pixels: each difference x_k - y_k of the
+// original values (exact products by powers of 2) with one rounding, the sum
+// of squares <= 4u, the approximate square root <= 2u (checked over every
+// float by the test suite): relative error <= 8u, plus an absolute 2^-62
+// where a tiny difference underflows.
+__device__ __forceinline__ float l2term32f(const float4 a, const float4 b)
+{
+    const float e0 = fmaf(a.x, a.w, -(b.x * b.w)), e1 = fmaf(a.y, a.w, -(b.y * b.w)), e2 = fmaf(a.z, a.w, -(b.z * b.w));
+    const float e = fmaf(e2, e2, fmaf(e1, e1, e0 * e0));
     float r;
     asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(e));
     return r;

@@ -146,23 +146,24 @@ constexpr float kSafety = 2.0f;   // factor applied to every analytic FP32 bound
 
 // Relative bound of Omega^4 for the exact and chromaticity modes (the
 // angular and L2 aggregate bounds of score32 below, a of them and 4 - a).
-template <int R, int DIST>
+template <int R, int DIST, bool F32IN = false>
 __device__ __forceinline__ float pow4_erel(int a)
 {
     constexpr float S = 4.0f * R;
-    constexpr float relA = (DIST == RGB ? 13.0f + S : 16.0f + S) * kU;
-    constexpr float relL = (6.0f + S) * kU;
+    constexpr float relA = (DIST == RGB ? 13.0f + S : (F32IN ? 24.0f : 16.0f) + S) * kU;
+    constexpr float relL = ((F32IN ? 8.0f : 6.0f) + S) * kU;
     return kSafety * (a * relA + (4 - a) * relL + 3.0f * kU);
 }
 
-template <int R, int FILTER, int DIST>
+template <int R, int FILTER, int DIST, bool F32IN = false>
 __device__ __forceinline__ float2 score32(float sa, float sl, float p, int quarter)
 {
     constexpr int NW = (2 * R + 1) * (2 * R + 1);
     constexpr float S = 4.0f * R;
+    constexpr float kA = F32IN ? 24.0f : 16.0f, kL = F32IN ? 8.0f : 6.0f;   // term bounds, float / integer input
     if (FILTER == BVDF) {
         float E;
-        if (DIST == EXACT) E = (16.0f + S) * kU * sa;
+        if (DIST == EXACT) E = (kA + S) * kU * sa;
         else if (DIST == RGB) E = (11.0f + S) * kU * sa;
         else E = 24.0f * NW * kU + S * kU * (fabsf(sa) + NW * 2e-4f);
         return make_float2(sa, kSafety * E);
@@ -170,7 +171,7 @@ __device__ __forceinline__ float2 score32(float sa, float sl, float p, int quart
     // DDF, log2 domain
     float relA;
     bool unsure = false;
-    if (DIST == EXACT) relA = (16.0f + S) * kU;
+    if (DIST == EXACT) relA = (kA + S) * kU;
     else if (DIST == RGB) relA = (13.0f + S) * kU;
     else {
         const float absA = 24.0f * NW * kU + S * kU * (fabsf(sa) + NW * 2e-4f);
@@ -178,7 +179,7 @@ __device__ __forceinline__ float2 score32(float sa, float sl, float p, int quart
         relA = absA / fmaxf(sa, 1e-30f);
     }
     if (unsure) return make_float2(-1e30f, INFINITY);   // Method 1 sum too close to 0 to take its log
-    const float relL = (6.0f + S) * kU;
+    const float relL = (kL + S) * kU;
     if (quarter >= 0) {
         // p = a/4: Omega^4 = SA^a SL^(4-a) orders like Omega, with a relative
         // bound (a relA + (4-a) relL + 3 roundings) and no logarithm
@@ -192,7 +193,7 @@ __device__ __forceinline__ float2 score32(float sa, float sl, float p, int quart
         default: g = pow4_product<4>(sa0, sl); break;
         }
         if (g == 0.0f) return make_float2(0.0f, 0.0f);   // an aggregate is exactly 0
-        if constexpr (DIST != MINIMAX) return make_float2(g, g * pow4_erel<R, DIST>(quarter));
+        if constexpr (DIST != MINIMAX) return make_float2(g, g * pow4_erel<R, DIST, F32IN>(quarter));
         return make_float2(g, kSafety * g * (quarter * relA + (4 - quarter) * relL + 3.0f * kU));
     }
     constexpr float kLg2Abs = 1.6e-7f;   // __log2f on [1,2): 2^-22.6
@@ -250,6 +251,10 @@ __device__ __forceinline__ typename C::PlaneT pair_term(const typename C::Pix &a
         }
         if constexpr (C::FILTER == DDF) t = make_double2(ang, l2);
         else t = ang;
+    } else if constexpr (C::F32IN) {
+        // float input, exact mode: normalised pixels (see normalize_f32)
+        if constexpr (C::FILTER == DDF) t = make_float2(angle32f(a, b), l2term32f(a, b));
+        else t = angle32f(a, b);
     } else {
         const PairInts r = pair_ints(a, b);
         float ang;
@@ -666,7 +671,7 @@ __device__ __forceinline__ unsigned bit_mask(P pred)
 // mask wide(), and the provisional choice is argmin().
 template <class C, class ZeroF, class WideF, class ArgF>
 __device__ __forceinline__ int resolve_near(unsigned near, const TileParams &prm, const typename C::Pix *pix,
-                                            const unsigned *keys, int ty, int tx, int gy, int gx, ZeroF zero,
+                                            const unsigned *keys, int b, int ty, int tx, int gy, int gx, ZeroF zero,
                                             WideF wide, ArgF argmin)
 {
     constexpr int R = C::R, W = C::W, NW = C::NW, PXW = C::PXW;
@@ -678,8 +683,18 @@ __device__ __forceinline__ int resolve_near(unsigned near, const TileParams &prm
     unsigned same = 0;
 #pragma unroll
     for (int k = 0; k < NW; ++k) same |= (keys[base + (k / W) * PXW + k % W] == rkey ? 1u : 0u) << k;
+    if constexpr (C::F32IN) {
+        // float keys are hashes: equal keys are confirmed on the pixel values
+        const float4 ref = pix[base + (first / W) * PXW + first % W];
+#pragma unroll 1
+        for (unsigned m = near & same; m; m &= m - 1) {
+            const int k = __ffs(m) - 1;
+            const float4 xk = pix[base + (k / W) * PXW + k % W];
+            if (!(xk.x == ref.x && xk.y == ref.y && xk.z == ref.z && xk.w == ref.w)) same &= ~(1u << k);
+        }
+    }
     bool equal = (near & ~same) == 0;
-    if constexpr (C::FILTER == BVDF) {
+    if constexpr (C::FILTER == BVDF && !C::F32IN) {
         if (!equal) {
             // same direction: integer cross product is 0, both non-zero
             const float4 ref = pix[base + (first / W) * PXW + first % W];
@@ -705,7 +720,8 @@ __device__ __forceinline__ int resolve_near(unsigned near, const TileParams &prm
     if (equal) return ((near >> C::CENTRE) & 1u) ? C::CENTRE : first;
     const unsigned mask = wide();
     const unsigned slot = atomicAdd(prm.recheck_ctr, 1u);
-    if (slot < prm.recheck_cap) prm.recheck_list[slot] = make_int2(prm.pix_base + gy * prm.N + gx, (int)mask);
+    if (slot < prm.recheck_cap)
+        prm.recheck_list[slot] = make_int2(prm.pix_base + ((C::F32IN ? b : 0) * prm.M + gy) * prm.N + gx, (int)mask);
     else atomicOr(prm.recheck_ctr + 1, 1u);
     return argmin();
 }
@@ -716,7 +732,7 @@ __device__ __forceinline__ int resolve_near(unsigned near, const TileParams &prm
 template <class C>
 __device__ __forceinline__ void select_and_store(const TileParams &prm, int b, int x0, int y0, int tid,
                                                  const typename C::Pix *pix, const unsigned *keys,
-                                                 const typename C::HwT *hw)
+                                                 const typename C::HwT *hw, bool unsafe_tile = false)
 {
     constexpr int R = C::R, W = C::W, NW = C::NW, PXW = C::PXW;
     using Pix = typename C::Pix;
@@ -735,6 +751,19 @@ __device__ __forceinline__ void select_and_store(const TileParams &prm, int b, i
             const float p4 = 4.0f * (float)prm.p;
             if (p4 == rintf(p4)) quarter = (int)p4;
         }
+        // Float input: the bounds also carry absolute parts (underflow of
+        // tiny products, at most 2^-53 in an aggregate), negligible against
+        // aggregates >= 2^-23.  A window with a smaller aggregate, or in a
+        // tile with an unsafe pixel, is decided by the FP64 recheck over all
+        // its members (unless they are all identical).
+        constexpr unsigned ALL = (NW == 32) ? 0xffffffffu : ((1u << NW) - 1u);
+        bool unsure = false;
+        if constexpr (C::F32IN) {
+            float am[NW];
+#pragma unroll
+            for (int k = 0; k < NW; ++k) am[k] = C::FILTER == DDF ? fminf(f[k].x, f[k].y) : f[k].x;
+            unsure = unsafe_tile || tree_min<NW>(am) < 0x1p-23f;
+        }
         // Relative bounds (BVDF with the exact or chromaticity terms, and DDF
         // with p = quarter / 4 scored by Omega^4): E = g * erel, g >= 0
         bool relative = C::FILTER == BVDF && C::DIST != MINIMAX;
@@ -745,10 +774,10 @@ __device__ __forceinline__ void select_and_store(const TileParams &prm, int b, i
             if constexpr (C::FILTER == BVDF) {
 #pragma unroll
                 for (int k = 0; k < NW; ++k) g[k] = f[k].x;
-                erel = kSafety * ((C::DIST == RGB ? 11.0f : 16.0f) + 4.0f * R) * kU;
+                erel = kSafety * ((C::DIST == RGB ? 11.0f : (C::F32IN ? 24.0f : 16.0f)) + 4.0f * R) * kU;
             } else {
                 // the uniform switch keeps each unrolled loop branch-free
-                erel = pow4_erel<R, C::DIST>(quarter);
+                erel = pow4_erel<R, C::DIST, C::F32IN>(quarter);
                 auto fill = [&](auto a) {
 #pragma unroll
                     for (int k = 0; k < NW; ++k) {
@@ -772,9 +801,9 @@ __device__ __forceinline__ void select_and_store(const TileParams &prm, int b, i
             const float gmin = tree_min<NW>(g);
             const float up = 1.0f + 6.0f * kU;
             const float thr = gmin * ((1.0f + erel) / (1.0f - erel)) * up;
-            const unsigned near = bit_mask<NW>([&](int k) { return g[k] <= thr; });
+            const unsigned near = unsure ? ALL : bit_mask<NW>([&](int k) { return g[k] <= thr; });
             sel = resolve_near<C>(
-                near, prm, pix, keys, ty, tx, gy, gx, [&](int k) { return g[k] == 0.0f; },
+                near, prm, pix, keys, b, ty, tx, gy, gx, [&](int k) { return !C::F32IN && g[k] == 0.0f; },
                 [&]() {
                     // widened by 100x the FP64 tie tolerance (1e-11: relative
                     // with floor 1e-3 for BVDF; in the log domain for DDF, a
@@ -782,7 +811,7 @@ __device__ __forceinline__ void select_and_store(const TileParams &prm, int b, i
                     const float U = gmin * (1.0f + erel);
                     const float delta = (C::FILTER == BVDF) ? 1e-9f * fmaxf(U, 1e-3f) + 1e-12f : 4e-9f * U;
                     const float thw = (U + delta) / (1.0f - erel) * up;
-                    return bit_mask<NW>([&](int k) { return g[k] <= thw; });
+                    return unsure ? ALL : bit_mask<NW>([&](int k) { return g[k] <= thw; });
                 },
                 [&]() {
                     // provisional choice (the recheck replaces it); the running
@@ -805,20 +834,21 @@ __device__ __forceinline__ void select_and_store(const TileParams &prm, int b, i
             for (int k = 0; k < NW; ++k) {
                 float sa = f[k].x;
                 if constexpr (C::FILTER == DDF && C::DIST == RGB) sa = fmaf(kSlope32, sa, (float)NW * kOffset32);
-                v[k] = score32<R, C::FILTER, C::DIST>(sa, f[k].y, (float)prm.p, quarter);
+                v[k] = score32<R, C::FILTER, C::DIST, C::F32IN>(sa, f[k].y, (float)prm.p, quarter);
             }
             // U = min (f + E); the near set {f - E <= U} holds every true minimiser
             float hi[NW];
 #pragma unroll
             for (int k = 0; k < NW; ++k) hi[k] = v[k].x + v[k].y;
             const float U = tree_min<NW>(hi);
-            const unsigned near = bit_mask<NW>([&](int k) { return v[k].x - v[k].y <= U; });
+            const unsigned near = unsure ? ALL : bit_mask<NW>([&](int k) { return v[k].x - v[k].y <= U; });
             sel = resolve_near<C>(
-                near, prm, pix, keys, ty, tx, gy, gx,
+                near, prm, pix, keys, b, ty, tx, gy, gx,
                 [&](int k) {
-                    // exact zeros: f == 0 (or -inf) with a zero bound
-                    return (v[k].y == 0.0f) && ((C::FILTER == DDF && (v[k].x == -INFINITY || v[k].x == 0.0f)) ||
-                                                (C::FILTER == BVDF && C::DIST != MINIMAX && v[k].x == 0.0f));
+                    // exact zeros: f == 0 (or -inf) with a zero bound (integer input only)
+                    return !C::F32IN && (v[k].y == 0.0f) &&
+                           ((C::FILTER == DDF && (v[k].x == -INFINITY || v[k].x == 0.0f)) ||
+                            (C::FILTER == BVDF && C::DIST != MINIMAX && v[k].x == 0.0f));
                 },
                 [&]() {
                     // widened by 100x the FP64 tie tolerance (1e-11: relative for
@@ -827,7 +857,7 @@ __device__ __forceinline__ void select_and_store(const TileParams &prm, int b, i
                     const float delta = (C::FILTER == BVDF) ? 1e-9f * fmaxf(fabsf(U), 1e-3f) + 1e-12f
                                         : quarter >= 0   ? 4e-9f * fabsf(U)
                                                          : 1e-9f;
-                    return bit_mask<NW>([&](int k) { return v[k].x - v[k].y <= U + delta; });
+                    return unsure ? ALL : bit_mask<NW>([&](int k) { return v[k].x - v[k].y <= U + delta; });
                 },
                 [&]() {
                     // provisional choice (the recheck replaces it); the running
@@ -848,9 +878,11 @@ __device__ __forceinline__ void select_and_store(const TileParams &prm, int b, i
     if constexpr (C::F32IN) {
         const size_t plane = (size_t)prm.M * prm.N;
         float *o = (float *)prm.out + (size_t)b * 3 * plane + lin;
-        o[0] = v.x;
-        o[plane] = v.y;
-        o[2 * plane] = v.z;
+        // FP32: the pixel is held normalised ({x 2^-k, 2^k}); the product is exact
+        const float sc = C::FP64 ? 1.0f : v.w;
+        o[0] = v.x * sc;
+        o[plane] = v.y * sc;
+        o[2 * plane] = v.z * sc;
         if (prm.idx) prm.idx[(size_t)b * plane + lin] = (int8_t)sel;
     } else {
         uint8_t *o = (uint8_t *)prm.out + 3 * lin;
@@ -878,6 +910,7 @@ __device__ __forceinline__ void tile_body(const TileParams &prm, int b, int x0, 
 
     const int tid = threadIdx.x;
 
+    bool unsafe = false;   // float input, FP32: the tile holds a pixel the FP32 bounds do not cover
     // 1. pixels of C plus a 2R column margin on each side, edge-replicated;
     //    every load of a thread is issued before the first is used (one
     //    memory round trip per tile)
@@ -893,12 +926,24 @@ __device__ __forceinline__ void tile_body(const TileParams &prm, int b, int x0, 
         for (int k = 0; k < PER; ++k) {
             const int i = tid + k * NTL;
             if (i >= NP) continue;
-            pix[i] = v[k];
-            if constexpr (!C::FP64) keys[i] = (unsigned)v[k].x | ((unsigned)v[k].y << 8) | ((unsigned)v[k].z << 16);
-            if constexpr (C::AUX) aux[i] = make_aux<C::DIST>(v[k]);
+            if constexpr (!C::FP64 && C::F32IN) {
+                // float input: normalised pixel, a hash of its bits as the key
+                // (equal keys are confirmed on the values), the unsafe flag
+                bool safe;
+                pix[i] = normalize_f32(v[k].x, v[k].y, v[k].z, safe);
+                keys[i] = (unsigned)__float_as_int(v[k].x) * 0x9E3779B1u ^
+                          (unsigned)__float_as_int(v[k].y) * 0x85EBCA77u ^ (unsigned)__float_as_int(v[k].z) * 0xC2B2AE3Du;
+                unsafe = unsafe || !safe;
+            } else {
+                pix[i] = v[k];
+                if constexpr (!C::FP64)
+                    keys[i] = (unsigned)v[k].x | ((unsigned)v[k].y << 8) | ((unsigned)v[k].z << 16);
+                if constexpr (C::AUX) aux[i] = make_aux<C::DIST>(v[k]);
+            }
         }
     }
-    __syncthreads();
+    if constexpr (!C::FP64 && C::F32IN) unsafe = __syncthreads_or(unsafe) != 0;
+    else __syncthreads();
 
     // 2. aggregates of the n windows containing this thread's pixel
     const int cy = tid / CW, cx = tid % CW;
@@ -957,7 +1002,7 @@ __device__ __forceinline__ void tile_body(const TileParams &prm, int b, int x0, 
     }
     bool selects = tid < C::TW * C::TH;
     if constexpr (!C::FP64) selects = selects && !prm.dbg_fe;
-    if (selects) select_and_store<C>(prm, b, x0, y0, tid, pix, keys, hw);
+    if (selects) select_and_store<C>(prm, b, x0, y0, tid, pix, keys, hw, unsafe);
 }
 
 
@@ -990,8 +1035,8 @@ cudaError_t launch_tile(const TileParams &prm, cudaStream_t st)
 // the FP64 tie tolerance; they cannot be selected or tie, and are given +inf.
 
 struct RecheckParams {
-    const uint8_t *img;
-    uint8_t *out;
+    const void *img;   // uint8 HWC, or float32 B x 3 x M x N
+    void *out;
     int8_t *idx;
     const int2 *list;
     const unsigned *ctr;
@@ -1013,23 +1058,33 @@ struct RecheckCfg {
 
 // Recheck of one listed pixel by one warp.  `base` is the warp's shared
 // memory (RecheckCfg::PER_WARP bytes, 16-byte aligned).
-template <int R, int FILTER, int DIST>
-__device__ __forceinline__ void recheck_pixel(const uint8_t *img, int M, int N, int lin, unsigned mask, uint8_t *out,
+// F32IN: img and out are float32 B x 3 x M x N and lin = (b M + y) N + x.
+template <int R, int FILTER, int DIST, bool F32IN = false>
+__device__ __forceinline__ void recheck_pixel(const void *img, int M, int N, int lin, unsigned mask, void *out,
                                               int8_t *idx, double p, int q, unsigned char *base, int lane)
 {
     using C = RecheckCfg<R, FILTER, DIST>;
+    using PixT = typename std::conditional<F32IN, float4, int4>::type;
     constexpr int W = C::W, NW = C::NW;
-    int4 *px = reinterpret_cast<int4 *>(base);
+    PixT *px = reinterpret_cast<PixT *>(base);
     double *Ma = reinterpret_cast<double *>(base + sizeof(int4) * NW);
     double *Ml = Ma + NW * NW;
     double *fs = Ma + C::MATS * NW * NW;
-    const int gy = lin / N, gx = lin % N;
+    const size_t plane = (size_t)M * N;
+    const int b = F32IN ? (int)(lin / plane) : 0;
+    const int pl = lin - (int)(b * plane);
+    const int gy = pl / N, gx = pl % N;
     for (int k = lane; k < NW; k += 32) {
         const int yy = min(max(gy + k / W - R, 0), M - 1);
         const int xx = min(max(gx + k % W - R, 0), N - 1);
-        const uint8_t *s = img + 3 * ((size_t)yy * N + xx);
-        const int x = s[0], y = s[1], z = s[2];
-        px[k] = make_int4(x, y, z, x * x + y * y + z * z);
+        if constexpr (F32IN) {
+            const float *s = (const float *)img + (size_t)b * 3 * plane + (size_t)yy * N + xx;
+            px[k] = make_float4(s[0], s[plane], s[2 * plane], 0.0f);
+        } else {
+            const uint8_t *s = (const uint8_t *)img + 3 * ((size_t)yy * N + xx);
+            const int x = s[0], y = s[1], z = s[2];
+            px[k] = make_int4(x, y, z, x * x + y * y + z * z);
+        }
     }
     __syncwarp();
     // rows of the masked members: terms (i, j) for i in mask, all j
@@ -1039,8 +1094,13 @@ __device__ __forceinline__ void recheck_pixel(const uint8_t *img, int M, int N, 
         unsigned mm = mask;
         for (int s = 0; s < r; ++s) mm &= mm - 1;   // drop the r lowest members
         const int i = __ffs(mm) - 1;
-        Ma[i * NW + j] = aterm64<DIST>(px[i], px[j], q);
-        if constexpr (FILTER == DDF) Ml[i * NW + j] = l2term64(px[i], px[j]);
+        if constexpr (F32IN) {
+            Ma[i * NW + j] = aterm64f(px[i], px[j]);
+            if constexpr (FILTER == DDF) Ml[i * NW + j] = l2term64f(px[i], px[j]);
+        } else {
+            Ma[i * NW + j] = aterm64<DIST>(px[i], px[j], q);
+            if constexpr (FILTER == DDF) Ml[i * NW + j] = l2term64(px[i], px[j]);
+        }
     }
     __syncwarp();
     if (lane < NW) {
@@ -1071,17 +1131,24 @@ __device__ __forceinline__ void recheck_pixel(const uint8_t *img, int M, int N, 
     __syncwarp();
     if (lane == 0) {
         const int sel = select64<FILTER, NW>([&](int k) { return fs[k]; });
-        const int4 v = px[sel];
-        uint8_t *o = out + 3 * (size_t)lin;
-        o[0] = (uint8_t)v.x;
-        o[1] = (uint8_t)v.y;
-        o[2] = (uint8_t)v.z;
+        const PixT v = px[sel];
+        if constexpr (F32IN) {
+            float *o = (float *)out + (size_t)b * 3 * plane + pl;
+            o[0] = v.x;
+            o[plane] = v.y;
+            o[2 * plane] = v.z;
+        } else {
+            uint8_t *o = (uint8_t *)out + 3 * (size_t)lin;
+            o[0] = (uint8_t)v.x;
+            o[1] = (uint8_t)v.y;
+            o[2] = (uint8_t)v.z;
+        }
         if (idx) idx[lin] = (int8_t)sel;
     }
     __syncwarp();
 }
 
-template <int R, int FILTER, int DIST>
+template <int R, int FILTER, int DIST, bool F32IN>
 __global__ void __launch_bounds__(128) recheck_kernel(const RecheckParams prm)
 {
     using C = RecheckCfg<R, FILTER, DIST>;
@@ -1092,23 +1159,23 @@ __global__ void __launch_bounds__(128) recheck_kernel(const RecheckParams prm)
     const int nwarps = gridDim.x * C::WARPS;
     for (unsigned it = blockIdx.x * C::WARPS + wid; it < count; it += nwarps) {
         const int2 ent = prm.list[it];
-        recheck_pixel<R, FILTER, DIST>(prm.img, prm.M, prm.N, ent.x, (unsigned)ent.y, prm.out, prm.idx, prm.p, prm.q,
-                                       base, lane);
+        recheck_pixel<R, FILTER, DIST, F32IN>(prm.img, prm.M, prm.N, ent.x, (unsigned)ent.y, prm.out, prm.idx, prm.p,
+                                              prm.q, base, lane);
     }
 }
 
-template <int R, int FILTER, int DIST>
+template <int R, int FILTER, int DIST, bool F32IN = false>
 cudaError_t launch_recheck(const RecheckParams &prm, int blocks, cudaStream_t st)
 {
     using C = RecheckCfg<R, FILTER, DIST>;
     static bool configured = false;
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(recheck_kernel<R, FILTER, DIST>,
+        cudaError_t e = cudaFuncSetAttribute(recheck_kernel<R, FILTER, DIST, F32IN>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    recheck_kernel<R, FILTER, DIST><<<blocks, 32 * C::WARPS, C::SMEM, st>>>(prm);
+    recheck_kernel<R, FILTER, DIST, F32IN><<<blocks, 32 * C::WARPS, C::SMEM, st>>>(prm);
     return cudaGetLastError();
 }
 

@@ -49,10 +49,13 @@ def lib():
             L.vdf_workspace_stats.argtypes = [P, P, P, P]
             L.vdf_debug_fp32_scores.argtypes = [P, i, i, i, i, d, i, i, P, P]
             L.vdf_debug_fp32_terms.argtypes = [P, i, i, i, P, P, P]
+            L.vdf_debug_fp32_terms_f32.argtypes = [P, i, P, P, P]
+            L.vdf_debug_sqrt_error.argtypes = [P, P]
             L.vdf_host_frames_buffer_bytes.argtypes, L.vdf_host_frames_buffer_bytes.restype = [i, i, i], sz
             L.vdf_filter_host_frames.argtypes = [P, P, P, i, i, i, i, i, d, i, i, i, P, sz, P]
             for f in ("vdf_filter", "vdf_filter_host", "vdf_workspace_stats", "vdf_debug_fp32_scores",
-                      "vdf_debug_fp32_terms", "vdf_filter_host_frames",
+                      "vdf_debug_fp32_terms", "vdf_filter_host_frames", "vdf_debug_fp32_terms_f32",
+                      "vdf_debug_sqrt_error",
                       "vdf_fp32_pass", "vdf_fp64_recheck", "vdf_filter_f32", "vdf_backward_f32"):
                 getattr(L, f).restype = i
             _lib = L
@@ -206,6 +209,27 @@ def debug_fp32_terms(pairs: torch.Tensor, dist="exact", q=4, stream=None):
     l2 = torch.empty(n, dtype=torch.float32, device=pairs.device)
     _check(lib().vdf_debug_fp32_terms(_ptr(pairs), n, _code(DISTS, dist), q, _ptr(ang), _ptr(l2), _stream(stream)))
     return ang, l2
+
+
+def debug_fp32_terms_f32(pairs: torch.Tensor, stream=None):
+    """FP32 terms of the float-input tile kernel for an (n, 6) float32 CUDA
+    tensor of pixel pairs.  Returns ``(angle, l2)`` (NaN for unsafe pixels)."""
+    if not (pairs.is_cuda and pairs.dtype == torch.float32 and pairs.dim() == 2 and pairs.shape[1] == 6):
+        raise VdfError("pairs must be a CUDA float32 tensor of shape (n, 6)")
+    pairs = pairs.contiguous()
+    n = int(pairs.shape[0])
+    ang = torch.empty(n, dtype=torch.float32, device=pairs.device)
+    l2 = torch.empty(n, dtype=torch.float32, device=pairs.device)
+    _check(lib().vdf_debug_fp32_terms_f32(_ptr(pairs), n, _ptr(ang), _ptr(l2), _stream(stream)))
+    return ang, l2
+
+
+def debug_sqrt_error(stream=None) -> float:
+    """Largest relative error (units of 2^-24) of the approximate square root
+    over every positive normal float."""
+    out = torch.zeros(1, dtype=torch.float32, device="cuda")
+    _check(lib().vdf_debug_sqrt_error(_ptr(out), _stream(stream)))
+    return float(out.item())
 
 
 def filter_f32(img: torch.Tensor, win: int = 3, filter="ddf", p: float = 0.5, dist="exact", q: int = 4,

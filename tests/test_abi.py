@@ -78,3 +78,9 @@ def test_host_frames_arguments_checked_on_host(L):
     assert L.vdf_filter_host_frames(arr, arr, None, 0, 8, 8, 3, 0, 0.5, 0, 4, 1, None, 0, None) == 0
     one = L.vdf_host_buffer_bytes(8, 8, 1)
     assert L.vdf_host_frames_buffer_bytes(8, 8, 1) == 3 * ((one + 255) // 256 * 256)
+
+
+def test_float_debug_entries_checked_on_host(L):
+    assert L.vdf_debug_fp32_terms_f32(None, 4, None, None, None) == -1
+    assert L.vdf_debug_fp32_terms_f32(ctypes.c_void_p(0x10000), -1, None, None, None) == -1
+    assert L.vdf_debug_sqrt_error(None, None) == -1
