@@ -1,8 +1,9 @@
 """The directional filters as a differentiable torch operation.
 
 ``DirectionalFilterFn.apply(x, win, filter, p, dist, q, precision)`` filters a
-B x 3 x M x N float32 CUDA batch with the library's kernels and saves the
-selected-member index map; its backward pass scatters the upstream gradient
+B x 3 x M x N float32 CUDA batch with the library's kernels (by default the
+FP32 certified path with its FP64 recheck, which selects what the FP64 path
+selects) and saves the selected-member index map; its backward pass scatters the upstream gradient
 to the selected source pixels with the library's gather kernel.  Both passes
 run on the current CUDA stream.
 """
@@ -15,7 +16,7 @@ from . import vdf
 
 class DirectionalFilterFn(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, x, win=3, filter="ddf", p=0.5, dist="exact", q=4, precision="fp64"):
+    def forward(ctx, x, win=3, filter="ddf", p=0.5, dist="exact", q=4, precision="fp32"):
         y, idx = vdf.filter_f32(x, win, filter, p, dist, q, precision)
         ctx.save_for_backward(idx)
         ctx.win = win
@@ -29,7 +30,7 @@ class DirectionalFilterFn(torch.autograd.Function):
         return gx, None, None, None, None, None, None
 
 
-def directional_filter(x, win=3, filter="ddf", p=0.5, dist="exact", q=4, precision="fp64"):
+def directional_filter(x, win=3, filter="ddf", p=0.5, dist="exact", q=4, precision="fp32"):
     """Differentiable filter; returns the filtered batch (the index map is
     kept for the backward pass)."""
     y, _ = DirectionalFilterFn.apply(x, win, filter, p, dist, q, precision)

@@ -233,7 +233,7 @@ def debug_sqrt_error(stream=None) -> float:
 
 
 def filter_f32(img: torch.Tensor, win: int = 3, filter="ddf", p: float = 0.5, dist="exact", q: int = 4,
-               precision="fp64", out: torch.Tensor | None = None, index: torch.Tensor | None = None,
+               precision="fp32", out: torch.Tensor | None = None, index: torch.Tensor | None = None,
                workspace: torch.Tensor | None = None, stream=None):
     """Filter a B x 3 x M x N float32 CUDA batch.  Returns ``(out, index)``."""
     if not (img.is_cuda and img.dtype == torch.float32 and img.dim() == 4 and img.shape[1] == 3):
