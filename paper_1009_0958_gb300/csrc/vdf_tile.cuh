@@ -569,16 +569,24 @@ __device__ __forceinline__ void all_slices32(std::integer_sequence<int, D...>, c
         }
     }
     __syncthreads();
-    // windows q = p - e inside the tile and the image, as bit masks over ey and ex
-    unsigned vy = 0, vx = 0;
+    // windows q = p - e inside the tile and the image: bit (ey+R) W + (ex+R)
+    // of `valid` (rows of W bits where the window row is inside, and the
+    // inside columns repeated in every row)
+    constexpr int W = C::W;
+    constexpr unsigned ROW = (1u << W) - 1u;
+    unsigned rows = 0, cols = 0;
 #pragma unroll
     for (int e = -R; e <= R; ++e) {
         const int ty = cy - e - R, tx = cx - e - R;
-        if (ty >= 0 && ty < C::TH && y0 + ty < prm.M) vy |= 1u << (e + R);
-        if (tx >= 0 && tx < C::TW && x0 + tx < prm.N) vx |= 1u << (e + R);
+        if (ty >= 0 && ty < C::TH && y0 + ty < prm.M) rows |= ROW << ((e + R) * W);
+        if (tx >= 0 && tx < C::TW && x0 + tx < prm.N) cols |= 1u << (e + R);
     }
+    unsigned rep = 0;   // the column bits repeated in each row
+#pragma unroll
+    for (int i = 0; i < W; ++i) rep |= cols << (i * W);
+    const unsigned valid = rows & rep;
     auto emit = [&](int ey, int ex, const PT &a) {
-        if ((vy >> (ey + R)) & (vx >> (ex + R)) & 1u) {
+        if (valid & (1u << ((ey + R) * W + (ex + R)))) {
             const int slot = ((cy - ey - R) * C::TW + (cx - ex - R)) * C::NW + (ey + R) * C::W + (ex + R);
             if constexpr (C::FILTER == DDF) hw[slot] = a;
             else hw[slot] = make_float2(a, 0.0f);
