@@ -210,16 +210,15 @@ __device__ __forceinline__ float angle_core(float c2, float Dh, float guard)
 {
     const float m = fmaf(c2, Dh, guard);
     const float rs = rsqrtf(m);
-    const float ta = c2 * rs;   // sqrt(c2)/d = tan(theta)
-    const float tb = Dh * rs;   // d/sqrt(c2) = cot(theta)
-    const float t = fminf(ta, tb);
+    // t = min(tan, cot) = min(sqrt(c2)/d, d/sqrt(c2)) = min(c2, d^2) / sqrt(c2 d^2)
+    const float t = fminf(c2, Dh) * rs;
     const float s = t * t;
     float v = atan_q(7);
 #pragma unroll
     for (int k = 6; k >= 0; --k) v = fmaf(v, s, atan_q(k));
     const float a = t * v;
-    // ta >= tb: theta >= 45 deg (also a zero vector: both 0, theta = pi/2)
-    return (ta >= tb) ? (kHalfPi32 - a) : a;
+    // c2 >= d^2: theta >= 45 deg (also a zero vector: both 0, theta = pi/2)
+    return (c2 >= Dh) ? (kHalfPi32 - a) : a;
 }
 
 // Eq. (2) angle in FP32: theta = atan2(sqrt(c2), d) via t = min(tan, cot).
