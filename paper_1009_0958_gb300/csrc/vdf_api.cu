@@ -171,7 +171,7 @@ int vdf_fp64_recheck(const uint8_t *img, int M, int N, int win, int filter, doub
     rp.N = N;
     rp.p = p;
     rp.q = minimax_q;
-    return cuda_fail(vdf::run_recheck(rp, win / 2, filter, dist_mode, num_sms() * 4, (cudaStream_t)stream));
+    return cuda_fail(vdf::run_recheck(rp, win / 2, filter, dist_mode, num_sms() * 16, (cudaStream_t)stream));
 }
 
 int vdf_filter(const uint8_t *img, int M, int N, int win, int filter, double p, int dist_mode, int minimax_q,
@@ -282,7 +282,7 @@ int vdf_filter_f32(const float *img, int B, int M, int N, int win, int filter, d
         rp.N = N;
         rp.p = p;
         rp.q = minimax_q;
-        e = vdf::run_recheck(rp, win / 2, filter, dist_mode, num_sms() * 4, st, true);
+        e = vdf::run_recheck(rp, win / 2, filter, dist_mode, num_sms() * 16, st, true);
     }
     return cuda_fail(e);
 }

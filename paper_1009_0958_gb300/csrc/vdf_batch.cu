@@ -1,18 +1,21 @@
-// vdf_batch.cu -- batches of uneven images in one persistent launch.
+// vdf_batch.cu -- batches of uneven images, one persistent launch per tile
+// configuration present in the batch.
 //
-// Work items are (image, tile) pairs numbered image by image.  The tile
-// kernel runs one CTA per SM; each CTA takes the next item from an atomic
-// counter in the workspace, finds its image by binary search over the
-// images' first item numbers, and runs the FP32 tile body of that image's
-// configuration (window, filter, tile shape).  Every CTA has the block size of
-// the largest configuration; smaller configurations leave the surplus threads
-// idle but still meet every barrier.  Pixels whose minimum is not certified
-// are appended to one batch-wide recheck list, keyed by batch pixel offset,
-// and a second persistent kernel re-evaluates them in FP64 (one warp each).
-// No device-side wait exists: the work counter is only ever incremented.
+// Images are grouped by configuration (window, filter, tile shape from the
+// autotuner).  Work items are (image, tile) pairs numbered image by image
+// within a group.  Each group's tile kernel runs as many CTAs as fit on the
+// SMs at that configuration's occupancy (two per SM where its shared memory
+// and registers allow); each CTA takes the next item of its group from an
+// atomic counter in the workspace and runs the FP32 tile body.  Pixels whose
+// minimum is not certified are appended to one batch-wide recheck list, keyed
+// by batch pixel offset, and a second persistent kernel re-evaluates them in
+// FP64 (one warp each).  No device-side wait exists: the work counters are
+// only ever incremented.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+#include <array>
 #include <mutex>
 #include <vector>
 
@@ -29,17 +32,18 @@ struct BatchDesc {
     int8_t *idx;
     int M, N;
     int tiles_x;
-    int tile_base;   // first work item of this image
-    int pix_base;    // first batch pixel offset of this image
+    int tile_base;   // first work item of this image within its group
+    int pix_base;    // first batch pixel offset of this image (ascending over the descriptor array)
     int cfg;         // ((win/2 - 1) * 2 + filter) * kNumShapes32 + shape
     double p;
 };
 
 struct BatchParams {
-    const BatchDesc *desc;
+    const BatchDesc *desc;   // the group's descriptors (tile kernel) or all of them (recheck kernel)
     int count;
-    int total_tiles;
-    unsigned *ctr;   // [0] recheck count, [1] overflow, [2] next work item
+    int total_tiles;         // work items of the group
+    unsigned *ctr;           // [0] recheck count, [1] overflow
+    unsigned *next_item;     // the group's work counter
     int2 *list;
     unsigned cap;
     int q;
@@ -54,73 +58,95 @@ struct BCfg {
 };
 constexpr int kNumCfgs = 2 * 2 * kNumShapes32;
 
-template <int... I>
-constexpr size_t max_smem(std::integer_sequence<int, I...>)
-{
-    size_t m = 0;
-    ((m = BCfg<I>::C::SMEM > m ? BCfg<I>::C::SMEM : m), ...);
-    return m;
-}
-template <int... I>
-constexpr int max_threads(std::integer_sequence<int, I...>)
-{
-    int m = 0;
-    ((m = BCfg<I>::C::NT > m ? BCfg<I>::C::NT : m), ...);
-    return m;
-}
-constexpr size_t kBatchSmem = max_smem(std::make_integer_sequence<int, kNumCfgs>{});
-constexpr int kBatchThreads = max_threads(std::make_integer_sequence<int, kNumCfgs>{});
-
-// One configuration's tile body as a call of its own: each body gets its own
-// register allocation instead of the union of all twelve.
+// The persistent tile kernel of one configuration.
 template <int CFG>
-__device__ __noinline__ void run_item(const TileParams prm, int t, int tiles_x)
+__global__ void __launch_bounds__(BCfg<CFG>::C::NT, BCfg<CFG>::C::MINB) batch_kernel(const BatchParams bp)
 {
     using C = typename BCfg<CFG>::C;
     extern __shared__ __align__(16) unsigned char smem[];
-    tile_body<C, kBatchThreads>(prm, 0, (t % tiles_x) * C::TW, (t / tiles_x) * C::TH, smem);
-}
-
-template <int... I>
-__device__ __forceinline__ void dispatch_item(int cfg, const TileParams &prm, int t, int tiles_x, unsigned char *smem,
-                                              std::integer_sequence<int, I...>)
-{
-    ((cfg == I ? run_item<I>(prm, t, tiles_x) : void()), ...);
-}
-
-__global__ void __launch_bounds__(kBatchThreads, 1) batch_kernel(const BatchParams bp)
-{
-    extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ int s_item;
-    for (;;) {
-        if (threadIdx.x == 0) s_item = (int)atomicAdd(bp.ctr + 2, 1u);
-        __syncthreads();
-        const int item = s_item;
+    // The CTA's current item and the next one (taken from the queue one item
+    // ahead, so the atomic's round trip overlaps the current tile), and the
+    // current image: its descriptor and the first item past it.  A CTA's
+    // items only increase, so the image index only moves forward; most items
+    // fall in the image of the one before and need no descriptor load.
+    __shared__ int s_item[2];
+    __shared__ int s_img, s_end;
+    __shared__ BatchDesc s_desc;
+    if (threadIdx.x == 0) {
+        s_item[0] = (int)atomicAdd(bp.next_item, 1u);
+        s_img = -1;
+        s_end = 0;
+    }
+    for (int it = 0;; it ^= 1) {
+        __syncthreads();   // s_item[it] is published; the previous item is done with shared memory
+        const int item = s_item[it];
         if (item >= bp.total_tiles) break;
-        int lo = 0, hi = bp.count - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (bp.desc[mid].tile_base <= item) lo = mid;
-            else hi = mid - 1;
+        int next = 0;
+        if (threadIdx.x == 0) {
+            next = (int)atomicAdd(bp.next_item, 1u);
+            if (item >= s_end) {
+                int img = s_img, end = s_end;
+                while (item >= end) {
+                    ++img;
+                    end = img + 1 < bp.count ? bp.desc[img + 1].tile_base : bp.total_tiles;
+                }
+                s_img = img;
+                s_end = end;
+                s_desc = bp.desc[img];
+            }
         }
-        const BatchDesc d = bp.desc[lo];
+        __syncthreads();   // s_desc is current
         TileParams prm{};
-        prm.img = d.img;
-        prm.out = d.out;
-        prm.idx = d.idx;
+        prm.img = s_desc.img;
+        prm.out = s_desc.out;
+        prm.idx = s_desc.idx;
         prm.recheck_list = bp.list;
         prm.recheck_ctr = bp.ctr;
         prm.recheck_cap = bp.cap;
-        prm.pix_base = d.pix_base;
-        prm.M = d.M;
-        prm.N = d.N;
+        prm.pix_base = s_desc.pix_base;
+        prm.M = s_desc.M;
+        prm.N = s_desc.N;
         prm.B = 1;
-        prm.p = d.p;
+        prm.p = s_desc.p;
         prm.q = bp.q;
-        dispatch_item(d.cfg, prm, item - d.tile_base, d.tiles_x, smem, std::make_integer_sequence<int, kNumCfgs>{});
-        __syncthreads();   // the next item reuses shared memory and s_item
+        const int t = item - s_desc.tile_base, tiles_x = s_desc.tiles_x;
+        tile_body<C, C::NT>(prm, 0, (t % tiles_x) * C::TW, (t / tiles_x) * C::TH, smem);
+        if (threadIdx.x == 0) s_item[it ^ 1] = next;
     }
 }
+
+// Launch of one group's kernel: one CTA per SM per resident CTA.
+template <int CFG>
+cudaError_t launch_group(const BatchParams &bp, int sms, cudaStream_t st)
+{
+    using C = typename BCfg<CFG>::C;
+    batch_kernel<CFG><<<sms * C::MINB, C::NT, C::SMEM, st>>>(bp);
+    return cudaGetLastError();
+}
+
+// Its shared-memory opt-in, set once for every configuration before any
+// launch (outside graph capture).
+template <int CFG>
+cudaError_t configure_group()
+{
+    return cudaFuncSetAttribute(batch_kernel<CFG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)BCfg<CFG>::C::SMEM);
+}
+
+using GroupLaunch = cudaError_t (*)(const BatchParams &, int, cudaStream_t);
+using GroupConfigure = cudaError_t (*)();
+template <int... I>
+constexpr std::array<GroupLaunch, sizeof...(I)> group_launchers(std::integer_sequence<int, I...>)
+{
+    return {&launch_group<I>...};
+}
+template <int... I>
+constexpr std::array<GroupConfigure, sizeof...(I)> group_configurers(std::integer_sequence<int, I...>)
+{
+    return {&configure_group<I>...};
+}
+constexpr auto kGroupLaunch = group_launchers(std::make_integer_sequence<int, kNumCfgs>{});
+constexpr auto kGroupConfigure = group_configurers(std::make_integer_sequence<int, kNumCfgs>{});
 
 // Per-warp shared memory of the largest recheck configuration.
 constexpr size_t kRecheckPerWarp = RecheckCfg<2, DDF, EXACT>::PER_WARP;
@@ -154,7 +180,9 @@ __global__ void __launch_bounds__(32 * kRecheckWarps) batch_recheck_kernel(const
     }
 }
 
+// recheck count, overflow flag, one work counter per configuration
 constexpr size_t kCtrBytes = 256;
+static_assert((2 + kNumCfgs) * sizeof(unsigned) <= kCtrBytes, "counters fit");
 
 size_t up16(size_t v) { return (v + 15) & ~(size_t)15; }
 
@@ -163,7 +191,12 @@ size_t up16(size_t v) { return (v + 15) & ~(size_t)15; }
 }  // namespace vdf
 
 struct vdf_plan {
-    std::vector<vdf::BatchDesc> desc;
+    // images of one configuration: descriptors first .. first + count - 1
+    struct Group {
+        int cfg, first, count, tiles;
+    };
+    std::vector<vdf::BatchDesc> desc;   // grouped by configuration
+    std::vector<Group> groups;
     int total_tiles = 0;
     long long total_pixels = 0;
     int q = 4;
@@ -189,7 +222,9 @@ size_t plan_ws_bytes(const vdf_plan *plan)
            sizeof(int2) * (size_t)plan->total_pixels;
 }
 
-vdf::BatchParams plan_params(const vdf_plan *plan, void *ws)
+// Parameters of group g's tile kernel, or (g < 0) of the recheck kernel over
+// all descriptors.
+vdf::BatchParams plan_params(const vdf_plan *plan, void *ws, int g)
 {
     vdf::BatchParams bp{};
     char *base = (char *)ws;
@@ -197,9 +232,15 @@ vdf::BatchParams plan_params(const vdf_plan *plan, void *ws)
     bp.desc = (const vdf::BatchDesc *)(base + vdf::kCtrBytes);
     bp.list = (int2 *)(base + vdf::kCtrBytes + vdf::up16(sizeof(vdf::BatchDesc) * plan->desc.size()));
     bp.count = (int)plan->desc.size();
-    bp.total_tiles = plan->total_tiles;
     bp.cap = (unsigned)plan->total_pixels;
     bp.q = plan->q;
+    if (g >= 0) {
+        const vdf_plan::Group &gr = plan->groups[g];
+        bp.desc += gr.first;
+        bp.count = gr.count;
+        bp.total_tiles = gr.tiles;
+        bp.next_item = bp.ctr + 2 + g;
+    }
     return bp;
 }
 
@@ -208,11 +249,9 @@ int set_attributes()
     static std::once_flag once;
     static cudaError_t err = cudaSuccess;
     std::call_once(once, [] {
-        err = cudaFuncSetAttribute(vdf::batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)vdf::kBatchSmem);
-        if (err == cudaSuccess)
-            err = cudaFuncSetAttribute(vdf::batch_recheck_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)(vdf::kRecheckPerWarp * vdf::kRecheckWarps));
+        err = cudaFuncSetAttribute(vdf::batch_recheck_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)(vdf::kRecheckPerWarp * vdf::kRecheckWarps));
+        for (int c = 0; c < vdf::kNumCfgs && err == cudaSuccess; ++c) err = vdf::kGroupConfigure[c]();
     });
     return err == cudaSuccess ? VDF_OK : VDF_E_CUDA;
 }
@@ -235,7 +274,7 @@ int vdf_plan_create(vdf_plan **plan, const vdf_image_desc *descs, int count, int
     if (!pl) return VDF_E_INVALID;
     pl->q = minimax_q;
     pl->sms = plan_num_sms();
-    long long tiles = 0, pixels = 0;
+    std::vector<vdf::BatchDesc> all;
     for (int i = 0; i < count; ++i) {
         const vdf_image_desc &d = descs[i];
         const size_t bytes = (size_t)d.M * d.N * 3;
@@ -248,27 +287,42 @@ int vdf_plan_create(vdf_plan **plan, const vdf_image_desc *descs, int count, int
             return VDF_E_INVALID;
         }
         const int shape = vdf_get_tuned_shape(d.win, d.filter, dist_mode);
-        const int tw = vdf::kShapes32[shape].tw, th = vdf::kShapes32[shape].th;
         vdf::BatchDesc bd{};
         bd.img = d.img;
         bd.out = d.out;
         bd.idx = d.index_out;
         bd.M = d.M;
         bd.N = d.N;
-        bd.tiles_x = (d.N + tw - 1) / tw;
-        bd.tile_base = (int)tiles;
-        bd.pix_base = (int)pixels;
+        bd.tiles_x = (d.N + vdf::kShapes32[shape].tw - 1) / vdf::kShapes32[shape].tw;
         bd.cfg = ((d.win / 2 - 1) * 2 + d.filter) * vdf::kNumShapes32 + shape;
         bd.p = d.p;
-        tiles += (long long)bd.tiles_x * ((d.M + th - 1) / th);
-        pixels += (long long)d.M * d.N;
-        if (tiles > (1LL << 31) - 1 || pixels > (1LL << 31) - 1) {
-            delete pl;
-            return VDF_E_INVALID;
-        }
-        pl->desc.push_back(bd);
+        all.push_back(bd);
     }
-    pl->total_tiles = (int)tiles;
+    // group by configuration (5x5 first), images in their given order within a group
+    long long tiles = 0, pixels = 0;
+    for (int cfg = vdf::kNumCfgs - 1; cfg >= 0; --cfg) {
+        vdf_plan::Group gr{cfg, (int)pl->desc.size(), 0, 0};
+        long long gtiles = 0;
+        const int th = vdf::kShapes32[cfg % vdf::kNumShapes32].th;
+        for (vdf::BatchDesc bd : all) {
+            if (bd.cfg != cfg) continue;
+            bd.tile_base = (int)gtiles;
+            bd.pix_base = (int)pixels;
+            gtiles += (long long)bd.tiles_x * ((bd.M + th - 1) / th);
+            pixels += (long long)bd.M * bd.N;
+            if (gtiles > (1LL << 31) - 1 || pixels > (1LL << 31) - 1) {
+                delete pl;
+                return VDF_E_INVALID;
+            }
+            pl->desc.push_back(bd);
+            ++gr.count;
+        }
+        if (gr.count == 0) continue;
+        gr.tiles = (int)gtiles;
+        tiles += gtiles;
+        pl->groups.push_back(gr);
+    }
+    pl->total_tiles = (int)std::min<long long>(tiles, (1LL << 31) - 1);
     pl->total_pixels = pixels;
     *plan = pl;
     return VDF_OK;
@@ -294,16 +348,14 @@ int vdf_filter_batch(vdf_plan *plan, void *workspace, size_t workspace_bytes, vo
     int rc = set_attributes();
     if (rc != VDF_OK) return rc;
     cudaStream_t st = (cudaStream_t)stream;
-    const vdf::BatchParams bp = plan_params(plan, workspace);
     const int sms = plan->sms;
-    cudaError_t e = cudaMemsetAsync(bp.ctr, 0, 4 * sizeof(unsigned), st);
-    if (e == cudaSuccess) {
-        vdf::batch_kernel<<<sms, vdf::kBatchThreads, vdf::kBatchSmem, st>>>(bp);
-        e = cudaGetLastError();
-    }
+    const int ngroups = (int)plan->groups.size();
+    cudaError_t e = cudaMemsetAsync(workspace, 0, (2 + ngroups) * sizeof(unsigned), st);
+    for (int g = 0; g < ngroups && e == cudaSuccess; ++g)
+        e = vdf::kGroupLaunch[plan->groups[g].cfg](plan_params(plan, workspace, g), sms, st);
     if (e == cudaSuccess) {
         vdf::batch_recheck_kernel<<<sms * 4, 32 * vdf::kRecheckWarps, vdf::kRecheckPerWarp * vdf::kRecheckWarps, st>>>(
-            bp);
+            plan_params(plan, workspace, -1));
         e = cudaGetLastError();
     }
     return e == cudaSuccess ? VDF_OK : VDF_E_CUDA;

@@ -1056,7 +1056,9 @@ struct RecheckParams {
 
 template <int R, int FILTER, int DIST>
 struct RecheckCfg {
-    static constexpr int W = 2 * R + 1, NW = W * W, WARPS = 4;
+    // one warp per block: consecutive list entries go to different SMs, whose
+    // FP64 pipes (1/64 of the FP32 rate) bound the recheck
+    static constexpr int W = 2 * R + 1, NW = W * W, WARPS = 1;
     static constexpr int MATS = (FILTER == DDF) ? 2 : 1;
     // per warp: int4 members first (16-byte aligned), then doubles; the size
     // is a multiple of 16 so every warp's region stays 16-byte aligned
@@ -1157,7 +1159,7 @@ __device__ __forceinline__ void recheck_pixel(const void *img, int M, int N, int
 }
 
 template <int R, int FILTER, int DIST, bool F32IN>
-__global__ void __launch_bounds__(128) recheck_kernel(const RecheckParams prm)
+__global__ void __launch_bounds__(32) recheck_kernel(const RecheckParams prm)
 {
     using C = RecheckCfg<R, FILTER, DIST>;
     extern __shared__ __align__(16) unsigned char smem[];
