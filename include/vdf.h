@@ -232,22 +232,33 @@ int vdf_get_tuned_shape(int win, int filter, int dist_mode);
 int vdf_set_tuned_shape(int win, int filter, int dist_mode, int shape);
 
 /*
- * Batches of uneven images in one persistent launch (FP32 certified path,
- * VDF_DIST_EXACT).  Each image has its own size, window (3 or 5), filter and
+ * Batches of uneven images (FP32 certified path, VDF_DIST_EXACT).  Each image has its own size, window (3 or 5), filter and
  * DDF exponent.  A plan holds, on the host, one descriptor per image with
  * the tile shape the autotuner table gives its configuration, and the tile
  * and pixel offsets of the batch.
  *   vdf_plan_create      validates the descriptors (the plan keeps a copy;
  *                        device pointers must stay valid while it is used).
- *   vdf_plan_workspace_bytes  device workspace: counters, descriptors and a
- *                        recheck list entry per pixel of the batch.
- *   vdf_plan_upload      copies the descriptors into `workspace` (once per
- *                        workspace, before vdf_filter_batch or a capture).
- *   vdf_filter_batch     zeroes the counters, launches one persistent tile
- *                        kernel (one CTA per SM; CTAs take (image, tile) work
- *                        items from an atomic counter) and one persistent FP64
- *                        recheck kernel.  Stream-ordered, no host sync, no
- *                        allocation: it can be captured in a CUDA graph.
+ *   vdf_plan_workspace_bytes  device workspace: counters, descriptors, the
+ *                        image index of every work item (4 bytes per tile) and
+ *                        a recheck list entry per pixel of the batch.
+ *   vdf_plan_upload      copies the descriptors and the item table into
+ *                        `workspace` (once per workspace, before
+ *                        vdf_filter_batch or a capture).
+ *   vdf_filter_batch     zeroes the counters, launches one tile kernel per
+ *                        configuration present (window, filter, tuned tile
+ *                        shape; each at its own block size and occupancy) over
+ *                        that configuration's (image, tile) work items, then
+ *                        one persistent FP64 recheck kernel.  Stream-ordered,
+ *                        no host sync, no allocation: it can be captured in a
+ *                        CUDA graph.
+ *   vdf_plan_set_persistent  selects the form of the tile kernels: 0 (the
+ *                        default) one CTA per work item, its image read from a
+ *                        per-item table in the workspace; 1 persistent, as
+ *                        many CTAs as fit on the SMs, each taking work items
+ *                        from an atomic counter.  Same results; the per-item
+ *                        form is the faster one (the persistent loop costs
+ *                        registers).  Drops a graph captured for the other
+ *                        form.
  *   vdf_plan_graph_launch  captures vdf_filter_batch into a CUDA graph on the
  *                        first call for a given workspace, then launches the
  *                        graph on `stream`.
@@ -271,6 +282,7 @@ size_t vdf_plan_workspace_bytes(const vdf_plan *plan);
 int vdf_plan_upload(vdf_plan *plan, void *workspace, size_t workspace_bytes, void *stream);
 int vdf_filter_batch(vdf_plan *plan, void *workspace, size_t workspace_bytes, void *stream);
 int vdf_plan_graph_launch(vdf_plan *plan, void *workspace, size_t workspace_bytes, void *stream);
+int vdf_plan_set_persistent(vdf_plan *plan, int persistent);
 void vdf_plan_destroy(vdf_plan *plan);
 
 /*

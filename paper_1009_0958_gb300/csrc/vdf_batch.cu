@@ -1,16 +1,23 @@
-// vdf_batch.cu -- batches of uneven images, one persistent launch per tile
+// vdf_batch.cu -- batches of uneven images, one tile-kernel launch per
 // configuration present in the batch.
 //
 // Images are grouped by configuration (window, filter, tile shape from the
 // autotuner).  Work items are (image, tile) pairs numbered image by image
-// within a group.  Each group's tile kernel runs as many CTAs as fit on the
-// SMs at that configuration's occupancy (two per SM where its shared memory
-// and registers allow); each CTA takes the next item of its group from an
-// atomic counter in the workspace and runs the FP32 tile body.  Pixels whose
-// minimum is not certified are appended to one batch-wide recheck list, keyed
-// by batch pixel offset, and a second persistent kernel re-evaluates them in
-// FP64 (one warp each).  No device-side wait exists: the work counters are
-// only ever incremented.
+// within a group.  A group's tile kernel takes one of two forms:
+//   * one CTA per work item (the default): the item's image comes from a
+//     per-item table in the workspace and the block scheduler hands out the
+//     items;
+//   * persistent: as many CTAs as fit on the SMs at the configuration's
+//     occupancy, each taking the next item of its group from an atomic
+//     counter in the workspace.
+// Both run the FP32 tile body of the configuration at its own block size and
+// occupancy (two CTAs per SM where shared memory and registers allow).  The
+// loop of the persistent form costs registers (DDF 5x5: 500 bytes of spills
+// against 44 in straight-line code), which makes it the slower of the two.
+// Pixels whose minimum is not certified are appended to one batch-wide
+// recheck list, keyed by batch pixel offset, and a persistent kernel
+// re-evaluates them in FP64 (one warp each).  No device-side wait exists: the
+// work counters are only ever incremented.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -43,7 +50,8 @@ struct BatchParams {
     int count;
     int total_tiles;         // work items of the group
     unsigned *ctr;           // [0] recheck count, [1] overflow
-    unsigned *next_item;     // the group's work counter
+    unsigned *next_item;     // the group's work counter (persistent form)
+    const int *item_image;   // the group's image of every work item (one-CTA-per-item form)
     int2 *list;
     unsigned cap;
     int q;
@@ -115,25 +123,59 @@ __global__ void __launch_bounds__(BCfg<CFG>::C::NT, BCfg<CFG>::C::MINB) batch_ke
     }
 }
 
-// Launch of one group's kernel: one CTA per SM per resident CTA.
+// The same work as one CTA per item: the item's image comes from the
+// per-item table, the block scheduler is the queue.  Straight-line code gets
+// the register allocation of the single-image tile kernel, which a loop
+// around the tile body does not.
 template <int CFG>
-cudaError_t launch_group(const BatchParams &bp, int sms, cudaStream_t st)
+__global__ void __launch_bounds__(BCfg<CFG>::C::NT, BCfg<CFG>::C::MINB) batch_item_kernel(const BatchParams bp)
 {
     using C = typename BCfg<CFG>::C;
-    batch_kernel<CFG><<<sms * C::MINB, C::NT, C::SMEM, st>>>(bp);
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int item = blockIdx.x;
+    const BatchDesc &d = bp.desc[bp.item_image[item]];
+    TileParams prm{};
+    prm.img = d.img;
+    prm.out = d.out;
+    prm.idx = d.idx;
+    prm.recheck_list = bp.list;
+    prm.recheck_ctr = bp.ctr;
+    prm.recheck_cap = bp.cap;
+    prm.pix_base = d.pix_base;
+    prm.M = d.M;
+    prm.N = d.N;
+    prm.B = 1;
+    prm.p = d.p;
+    prm.q = bp.q;
+    const int t = item - d.tile_base, tiles_x = d.tiles_x;
+    tile_body<C, C::NT>(prm, 0, (t % tiles_x) * C::TW, (t / tiles_x) * C::TH, smem);
+}
+
+// Launch of one group's kernel: persistent (one CTA per SM per resident
+// CTA), or one CTA per item.
+template <int CFG>
+cudaError_t launch_group(const BatchParams &bp, int sms, cudaStream_t st, bool persistent)
+{
+    using C = typename BCfg<CFG>::C;
+    if (persistent) batch_kernel<CFG><<<sms * C::MINB, C::NT, C::SMEM, st>>>(bp);
+    else batch_item_kernel<CFG><<<bp.total_tiles, C::NT, C::SMEM, st>>>(bp);
     return cudaGetLastError();
 }
 
-// Its shared-memory opt-in, set once for every configuration before any
-// launch (outside graph capture).
+// The shared-memory opt-in of both forms, set once for every configuration
+// before any launch (outside graph capture).
 template <int CFG>
 cudaError_t configure_group()
 {
-    return cudaFuncSetAttribute(batch_kernel<CFG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)BCfg<CFG>::C::SMEM);
+    cudaError_t e = cudaFuncSetAttribute(batch_item_kernel<CFG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)BCfg<CFG>::C::SMEM);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(batch_kernel<CFG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)BCfg<CFG>::C::SMEM);
+    return e;
 }
 
-using GroupLaunch = cudaError_t (*)(const BatchParams &, int, cudaStream_t);
+using GroupLaunch = cudaError_t (*)(const BatchParams &, int, cudaStream_t, bool);
 using GroupConfigure = cudaError_t (*)();
 template <int... I>
 constexpr std::array<GroupLaunch, sizeof...(I)> group_launchers(std::integer_sequence<int, I...>)
@@ -194,13 +236,16 @@ struct vdf_plan {
     // images of one configuration: descriptors first .. first + count - 1
     struct Group {
         int cfg, first, count, tiles;
+        long long item_first;   // its first entry of item_image
     };
     std::vector<vdf::BatchDesc> desc;   // grouped by configuration
     std::vector<Group> groups;
+    std::vector<int> item_image;        // per work item: its image within the group
     int total_tiles = 0;
     long long total_pixels = 0;
     int q = 4;
     int sms = 1;
+    bool persistent = false;   // tile kernels in the persistent work-queue form
     std::mutex mutex;
     cudaGraphExec_t exec = nullptr;
     void *exec_ws = nullptr;
@@ -216,10 +261,13 @@ int plan_num_sms()
     return sms > 0 ? sms : 1;
 }
 
+// Workspace: counters | descriptors | item table | recheck list.
+size_t desc_bytes(const vdf_plan *plan) { return vdf::up16(sizeof(vdf::BatchDesc) * plan->desc.size()); }
+size_t table_bytes(const vdf_plan *plan) { return vdf::up16(sizeof(int) * plan->item_image.size()); }
+
 size_t plan_ws_bytes(const vdf_plan *plan)
 {
-    return vdf::kCtrBytes + vdf::up16(sizeof(vdf::BatchDesc) * plan->desc.size()) +
-           sizeof(int2) * (size_t)plan->total_pixels;
+    return vdf::kCtrBytes + desc_bytes(plan) + table_bytes(plan) + sizeof(int2) * (size_t)plan->total_pixels;
 }
 
 // Parameters of group g's tile kernel, or (g < 0) of the recheck kernel over
@@ -230,7 +278,8 @@ vdf::BatchParams plan_params(const vdf_plan *plan, void *ws, int g)
     char *base = (char *)ws;
     bp.ctr = (unsigned *)base;
     bp.desc = (const vdf::BatchDesc *)(base + vdf::kCtrBytes);
-    bp.list = (int2 *)(base + vdf::kCtrBytes + vdf::up16(sizeof(vdf::BatchDesc) * plan->desc.size()));
+    const int *table = (const int *)(base + vdf::kCtrBytes + desc_bytes(plan));
+    bp.list = (int2 *)(base + vdf::kCtrBytes + desc_bytes(plan) + table_bytes(plan));
     bp.count = (int)plan->desc.size();
     bp.cap = (unsigned)plan->total_pixels;
     bp.q = plan->q;
@@ -240,6 +289,7 @@ vdf::BatchParams plan_params(const vdf_plan *plan, void *ws, int g)
         bp.count = gr.count;
         bp.total_tiles = gr.tiles;
         bp.next_item = bp.ctr + 2 + g;
+        bp.item_image = table + gr.item_first;
     }
     return bp;
 }
@@ -301,19 +351,21 @@ int vdf_plan_create(vdf_plan **plan, const vdf_image_desc *descs, int count, int
     // group by configuration (5x5 first), images in their given order within a group
     long long tiles = 0, pixels = 0;
     for (int cfg = vdf::kNumCfgs - 1; cfg >= 0; --cfg) {
-        vdf_plan::Group gr{cfg, (int)pl->desc.size(), 0, 0};
+        vdf_plan::Group gr{cfg, (int)pl->desc.size(), 0, 0, (long long)pl->item_image.size()};
         long long gtiles = 0;
         const int th = vdf::kShapes32[cfg % vdf::kNumShapes32].th;
         for (vdf::BatchDesc bd : all) {
             if (bd.cfg != cfg) continue;
             bd.tile_base = (int)gtiles;
             bd.pix_base = (int)pixels;
-            gtiles += (long long)bd.tiles_x * ((bd.M + th - 1) / th);
+            const long long nt = (long long)bd.tiles_x * ((bd.M + th - 1) / th);
+            gtiles += nt;
             pixels += (long long)bd.M * bd.N;
             if (gtiles > (1LL << 31) - 1 || pixels > (1LL << 31) - 1) {
                 delete pl;
                 return VDF_E_INVALID;
             }
+            pl->item_image.insert(pl->item_image.end(), (size_t)nt, gr.count);
             pl->desc.push_back(bd);
             ++gr.count;
         }
@@ -337,6 +389,9 @@ int vdf_plan_upload(vdf_plan *plan, void *workspace, size_t workspace_bytes, voi
     cudaError_t e = cudaMemcpyAsync((char *)workspace + vdf::kCtrBytes, plan->desc.data(),
                                     sizeof(vdf::BatchDesc) * plan->desc.size(), cudaMemcpyHostToDevice,
                                     (cudaStream_t)stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync((char *)workspace + vdf::kCtrBytes + desc_bytes(plan), plan->item_image.data(),
+                            sizeof(int) * plan->item_image.size(), cudaMemcpyHostToDevice, (cudaStream_t)stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
     return e == cudaSuccess ? VDF_OK : VDF_E_CUDA;
 }
@@ -352,7 +407,7 @@ int vdf_filter_batch(vdf_plan *plan, void *workspace, size_t workspace_bytes, vo
     const int ngroups = (int)plan->groups.size();
     cudaError_t e = cudaMemsetAsync(workspace, 0, (2 + ngroups) * sizeof(unsigned), st);
     for (int g = 0; g < ngroups && e == cudaSuccess; ++g)
-        e = vdf::kGroupLaunch[plan->groups[g].cfg](plan_params(plan, workspace, g), sms, st);
+        e = vdf::kGroupLaunch[plan->groups[g].cfg](plan_params(plan, workspace, g), sms, st, plan->persistent);
     if (e == cudaSuccess) {
         vdf::batch_recheck_kernel<<<sms * 4, 32 * vdf::kRecheckWarps, vdf::kRecheckPerWarp * vdf::kRecheckWarps, st>>>(
             plan_params(plan, workspace, -1));
@@ -395,6 +450,19 @@ int vdf_plan_graph_launch(vdf_plan *plan, void *workspace, size_t workspace_byte
         plan->exec_ws = workspace;
     }
     return cudaGraphLaunch(plan->exec, (cudaStream_t)stream) == cudaSuccess ? VDF_OK : VDF_E_CUDA;
+}
+
+int vdf_plan_set_persistent(vdf_plan *plan, int persistent)
+{
+    if (!plan) return VDF_E_INVALID;
+    std::lock_guard<std::mutex> lock(plan->mutex);
+    if (plan->persistent != (persistent != 0) && plan->exec) {
+        cudaGraphExecDestroy(plan->exec);   // the captured graph holds the other form
+        plan->exec = nullptr;
+        plan->exec_ws = nullptr;
+    }
+    plan->persistent = persistent != 0;
+    return VDF_OK;
 }
 
 void vdf_plan_destroy(vdf_plan *plan)

@@ -1116,7 +1116,7 @@ __device__ __forceinline__ void recheck_pixel(const void *img, int M, int N, int
     if (lane < NW) {
         double f = INFINITY;
         if ((mask >> lane) & 1u) {
-            const int ey = lane / W - R, ex = lane % W - R;
+            const int ey = lane / W - R;   // window offset (ey, ex), ex = lane % W - R
             double sa = 0.0, sl = 0.0;
             // dy order 0, +1, -1, +2, -2, ... restricted to the window's rows
             for (int s = 0; s <= 4 * R; ++s) {

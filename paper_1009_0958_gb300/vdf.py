@@ -348,15 +348,18 @@ class ImageDesc(ctypes.Structure):
 
 
 class Plan:
-    """A batch of uneven uint8 images filtered in one persistent launch.
+    """A batch of uneven uint8 images: one tile-kernel launch per
+    configuration present, then one FP64 recheck launch.
 
     ``items``: list of dicts with keys ``img`` (CUDA uint8 M x N x 3), and
     optionally ``win`` (3), ``filter`` ("bvdf"), ``p`` (0.5), ``out`` and
     ``index``.  Outputs are allocated when absent.  The workspace is
     allocated here (torch), uploaded once, and reused by every launch.
+    ``persistent`` selects the persistent work-queue form of the tile kernels
+    instead of one CTA per work item (same results, slower).
     """
 
-    def __init__(self, items, dist="exact", q=4, device=None):
+    def __init__(self, items, dist="exact", q=4, device=None, persistent=False):
         L = lib()
         if L.vdf_plan_create.argtypes is None:
             P, i, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t
@@ -367,6 +370,7 @@ class Plan:
                 getattr(L, f).restype = i
             L.vdf_plan_create.restype = i
             L.vdf_plan_destroy.argtypes, L.vdf_plan_destroy.restype = [P], None
+            L.vdf_plan_set_persistent.argtypes, L.vdf_plan_set_persistent.restype = [P, i], i
         self._L = L
         self.items = []
         descs = (ImageDesc * len(items))()
@@ -387,6 +391,7 @@ class Plan:
         self._handle = ctypes.c_void_p()
         _check(L.vdf_plan_create(ctypes.byref(self._handle), ctypes.cast(descs, ctypes.c_void_p), len(items),
                                  _code(DISTS, dist), q))
+        _check(L.vdf_plan_set_persistent(self._handle, int(bool(persistent))))
         nbytes = int(L.vdf_plan_workspace_bytes(self._handle))
         dev = device or self.items[0]["img"].device
         self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=dev)
@@ -395,6 +400,9 @@ class Plan:
 
     def run(self, stream=None):
         _check(self._L.vdf_filter_batch(self._handle, self._wp, self._wn, _stream(stream)))
+
+    def set_persistent(self, persistent: bool):
+        _check(self._L.vdf_plan_set_persistent(self._handle, int(bool(persistent))))
 
     def graph_launch(self, stream=None):
         _check(self._L.vdf_plan_graph_launch(self._handle, self._wp, self._wn, _stream(stream)))

@@ -1,6 +1,7 @@
-"""Batches of uneven images in one persistent launch, CUDA-graph replays and
-the tile-shape autotuner: every result must equal the single-image path (and
-the oracle on small images) bit for bit."""
+"""Batches of uneven images (one launch per configuration, in the per-item
+and the persistent work-queue forms), CUDA-graph replays and the tile-shape
+autotuner: every result must equal the single-image path (and the oracle on
+small images) bit for bit."""
 import numpy as np
 import pytest
 
@@ -46,11 +47,12 @@ def check_against_single(V, plan, prec="fp32"):
         assert torch.equal(o, it["out"]) and torch.equal(i, it["index"])
 
 
-@pytest.mark.parametrize("shapes", [(0, 0, 0, 0), (1, 2, 2, 1), (2, 1, 0, 2)])
-def test_batch_equals_single_image_calls(V, shapes):
+@pytest.mark.parametrize("persistent", [False, True])
+@pytest.mark.parametrize("shapes", [(0, 0, 0, 0), (1, 2, 2, 1), (2, 1, 0, 2), (3, 3, 3, 3)])
+def test_batch_equals_single_image_calls(V, shapes, persistent):
     for (win, f), s in zip([(3, "bvdf"), (3, "ddf"), (5, "bvdf"), (5, "ddf")], shapes):
         V.set_tuned_shape(win, f, "exact", s)
-    plan = V.Plan(batch_items(1, 24))
+    plan = V.Plan(batch_items(1, 24), persistent=persistent)
     plan.run()
     torch.cuda.synchronize()
     check_against_single(V, plan, "fp32")
@@ -59,10 +61,11 @@ def test_batch_equals_single_image_calls(V, shapes):
     assert overflow == 0 and rechecked > 0
 
 
-def test_batch_matches_oracle_on_small_images(V):
+@pytest.mark.parametrize("persistent", [False, True])
+def test_batch_matches_oracle_on_small_images(V, persistent):
     import oracle
     oracle.build()
-    plan = V.Plan(batch_items(2, 10, hi=48))
+    plan = V.Plan(batch_items(2, 10, hi=48), persistent=persistent)
     plan.run()
     torch.cuda.synchronize()
     for it in plan.items:
@@ -83,6 +86,13 @@ def test_graph_replay_tracks_input_contents(V):
         M, N = it["img"].shape[:2]
         it["img"].copy_(torch.from_numpy(synth.make_image(M, N, 777 + k, 0.2, rectangles=2)[1]).cuda())
     plan.graph_launch()
+    plan.graph_launch()
+    torch.cuda.synchronize()
+    check_against_single(V, plan)
+    # switching the form drops the captured graph; the new one gives the same
+    for it in plan.items:
+        it["out"].zero_()
+    plan.set_persistent(True)
     plan.graph_launch()
     torch.cuda.synchronize()
     check_against_single(V, plan)
