@@ -1097,19 +1097,39 @@ __device__ __forceinline__ void recheck_pixel(const void *img, int M, int N, int
         }
     }
     __syncwarp();
-    // rows of the masked members: terms (i, j) for i in mask, all j
+    // rows of the masked members: terms (i, j) for i in mask, all j.  The
+    // term functions are symmetric bit for bit, so a pair of two members is
+    // computed once (in the row of the lower one) and stored in both rows:
+    // the r-th lowest member's row holds every j except the r members below
+    // it, NW - r work items.
+    constexpr unsigned ALL = (NW == 32) ? 0xffffffffu : ((1u << NW) - 1u);
     const int cnt = __popc(mask);
-    for (int t = lane; t < cnt * NW; t += 32) {
-        const int r = t / NW, j = t % NW;
+    const int items = cnt * NW - cnt * (cnt - 1) / 2;
+    for (int t = lane; t < items; t += 32) {
+        int r = 0, start = 0;
+        while (start + (NW - r) <= t) {
+            start += NW - r;
+            ++r;
+        }
         unsigned mm = mask;
         for (int s = 0; s < r; ++s) mm &= mm - 1;   // drop the r lowest members
         const int i = __ffs(mm) - 1;
+        unsigned row = ALL & ~(mask & ((1u << i) - 1u));
+        for (int s = start; s < t; ++s) row &= row - 1;
+        const int j = __ffs(row) - 1;
+        double a, l = 0.0;
         if constexpr (F32IN) {
-            Ma[i * NW + j] = aterm64f(px[i], px[j]);
-            if constexpr (FILTER == DDF) Ml[i * NW + j] = l2term64f(px[i], px[j]);
+            a = aterm64f(px[i], px[j]);
+            if constexpr (FILTER == DDF) l = l2term64f(px[i], px[j]);
         } else {
-            Ma[i * NW + j] = aterm64<DIST>(px[i], px[j], q);
-            if constexpr (FILTER == DDF) Ml[i * NW + j] = l2term64(px[i], px[j]);
+            a = aterm64<DIST>(px[i], px[j], q);
+            if constexpr (FILTER == DDF) l = l2term64(px[i], px[j]);
+        }
+        Ma[i * NW + j] = a;
+        if constexpr (FILTER == DDF) Ml[i * NW + j] = l;
+        if (j != i && ((mask >> j) & 1u)) {
+            Ma[j * NW + i] = a;
+            if constexpr (FILTER == DDF) Ml[j * NW + i] = l;
         }
     }
     __syncwarp();
