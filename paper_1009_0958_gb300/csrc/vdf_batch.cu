@@ -192,7 +192,7 @@ constexpr auto kGroupConfigure = group_configurers(std::make_integer_sequence<in
 
 // Per-warp shared memory of the largest recheck configuration.
 constexpr size_t kRecheckPerWarp = RecheckCfg<2, DDF, EXACT>::PER_WARP;
-constexpr int kRecheckWarps = 4;
+constexpr int kRecheckWarps = 1;   // one warp per block, as the single-image recheck
 
 __global__ void __launch_bounds__(32 * kRecheckWarps) batch_recheck_kernel(const BatchParams bp)
 {
@@ -409,7 +409,7 @@ int vdf_filter_batch(vdf_plan *plan, void *workspace, size_t workspace_bytes, vo
     for (int g = 0; g < ngroups && e == cudaSuccess; ++g)
         e = vdf::kGroupLaunch[plan->groups[g].cfg](plan_params(plan, workspace, g), sms, st, plan->persistent);
     if (e == cudaSuccess) {
-        vdf::batch_recheck_kernel<<<sms * 4, 32 * vdf::kRecheckWarps, vdf::kRecheckPerWarp * vdf::kRecheckWarps, st>>>(
+        vdf::batch_recheck_kernel<<<sms * 16, 32 * vdf::kRecheckWarps, vdf::kRecheckPerWarp * vdf::kRecheckWarps, st>>>(
             plan_params(plan, workspace, -1));
         e = cudaGetLastError();
     }
