@@ -22,7 +22,9 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-FILTERS = {"bvdf": 0, "ddf": 1}
+FILTERS = {"bvdf": 0, "ddf": 1, "vmf": 2}
+# Minkowski order of Eq. (1): 1, 2, or "inf" (the maximum component difference)
+ORDERS = {1: 1, 2: 2, "inf": 0}
 DISTS = {"exact": 0, "minimax": 1, "rgb": 2}
 FLAG_ESCALATED, FLAG_TIE, FLAG_GRAY = 1, 2, 4
 
@@ -47,12 +49,15 @@ def lib():
             P = ctypes.c_void_p
             i, d, i64 = ctypes.c_int, ctypes.c_double, ctypes.c_int64
             L.vdf_oracle_filter_u8.argtypes = [P, i, i, i, i, d, i, i, P, i64, P, P, P, P, i]
+            L.vdf_oracle_filter_u8_lp.argtypes = [P, i, i, i, i, d, i, i, i, P, i64, P, P, P, P, i]
+            L.vdf_oracle_window_lp.argtypes = [P, i, i, d, i, i, i, P, P, P]
             L.vdf_oracle_filter_f32.argtypes = [P, i, i, i, i, i, d, i, i, P, i64, P, P, P, P, i]
             L.vdf_oracle_window.argtypes = [P, i, i, d, i, i, P, P, P]
             L.vdf_oracle_term.argtypes = [P, P, i, i, i, P, P, P]
             L.vdf_oracle_poly.argtypes = [i, i, d, P, P]
             L.vdf_oracle_max_threads.argtypes = []
-            for f in ("vdf_oracle_filter_u8", "vdf_oracle_filter_f32", "vdf_oracle_window",
+            for f in ("vdf_oracle_filter_u8", "vdf_oracle_filter_u8_lp", "vdf_oracle_window_lp",
+                      "vdf_oracle_filter_f32", "vdf_oracle_window",
                       "vdf_oracle_term", "vdf_oracle_poly", "vdf_oracle_max_threads"):
                 getattr(L, f).restype = ctypes.c_int
             _lib = L
@@ -67,12 +72,15 @@ def _cfg(filter, dist):
     return FILTERS[filter] if isinstance(filter, str) else int(filter), DISTS[dist] if isinstance(dist, str) else int(dist)
 
 
-def filter_u8(img, win=3, filter="bvdf", p=0.5, dist="exact", q=4, pixels=None, want_agg=False, threads=0):
+def filter_u8(img, win=3, filter="bvdf", p=0.5, dist="exact", q=4, pixels=None, want_agg=False, threads=0,
+              order=2):
     """Run the oracle on an M x N x 3 uint8 image.
 
-    Returns a dict with ``out`` (uint8, M x N x 3, or count x 3 for a pixel
-    subset), ``idx`` (int8), ``flags`` (int32) and, if requested, ``agg``
-    (float64, [..., n, 2]: sum of angular terms, sum of L2 terms).
+    ``order`` is the Minkowski order of the distance term (DDF, VMF): 1, 2
+    or "inf".  Returns a dict with ``out`` (uint8, M x N x 3, or count x 3
+    for a pixel subset), ``idx`` (int8), ``flags`` (int32) and, if requested,
+    ``agg`` (float64, [..., n, 2]: sum of angular terms, sum of distance
+    terms).
     """
     img = np.ascontiguousarray(img, dtype=np.uint8)
     M, N = img.shape[:2]
@@ -87,8 +95,8 @@ def filter_u8(img, win=3, filter="bvdf", p=0.5, dist="exact", q=4, pixels=None, 
     idx = np.zeros(shape, np.int8)
     flags = np.zeros(shape, np.int32)
     agg = np.zeros(shape + (n, 2), np.float64) if want_agg else None
-    rc = lib().vdf_oracle_filter_u8(_ptr(img), M, N, win, f, float(p), dm, q, _ptr(pix), count,
-                                   _ptr(out), _ptr(idx), _ptr(flags), _ptr(agg), threads)
+    rc = lib().vdf_oracle_filter_u8_lp(_ptr(img), M, N, win, f, float(p), ORDERS[order], dm, q, _ptr(pix), count,
+                                      _ptr(out), _ptr(idx), _ptr(flags), _ptr(agg), threads)
     if rc != 0:
         raise ValueError("oracle rejected the arguments")
     return {"out": out, "idx": idx, "flags": flags, "agg": agg}
@@ -122,7 +130,7 @@ def filter_f32(img_nchw, win=3, filter="ddf", p=0.5, dist="exact", q=4, pixels=N
     return {"out": out, "idx": idx, "flags": flags, "agg": agg}
 
 
-def window(vecs, filter="bvdf", p=0.5, dist="exact", q=4):
+def window(vecs, filter="bvdf", p=0.5, dist="exact", q=4, order=2):
     """Select within one window given as an n x 3 array (raster order).
 
     Returns ``(index, scores, agg, flags)``."""
@@ -132,19 +140,22 @@ def window(vecs, filter="bvdf", p=0.5, dist="exact", q=4):
     score = np.zeros(n, np.float64)
     agg = np.zeros((n, 2), np.float64)
     fl = np.zeros(1, np.int32)
-    sel = lib().vdf_oracle_window(_ptr(v), n, f, float(p), dm, q, _ptr(score), _ptr(agg), _ptr(fl))
+    sel = lib().vdf_oracle_window_lp(_ptr(v), n, f, float(p), ORDERS[order], dm, q, _ptr(score), _ptr(agg),
+                                     _ptr(fl))
     if sel < 0:
         raise ValueError("oracle rejected the arguments")
     return sel, score, agg, int(fl[0])
 
 
 def term(x, y, which="angle", dist="exact", q=4):
-    """One pair term: returns ``(double_value, binary128_hi, binary128_lo)``."""
+    """One pair term (``which``: "angle", "l2", "l1" or "linf"): returns
+    ``(double_value, binary128_hi, binary128_lo)``."""
     xa = np.ascontiguousarray(x, dtype=np.float64)
     ya = np.ascontiguousarray(y, dtype=np.float64)
     d, hi, lo = (np.zeros(1) for _ in range(3))
     _, dm = _cfg(0, dist)
-    rc = lib().vdf_oracle_term(_ptr(xa), _ptr(ya), 1 if which == "l2" else 0, dm, q, _ptr(d), _ptr(hi), _ptr(lo))
+    code = {"angle": 0, "l2": 1, "l1": 2, "linf": 3}[which]
+    rc = lib().vdf_oracle_term(_ptr(xa), _ptr(ya), code, dm, q, _ptr(d), _ptr(hi), _ptr(lo))
     if rc != 0:
         raise ValueError("bad term arguments")
     return float(d[0]), float(hi[0]), float(lo[0])

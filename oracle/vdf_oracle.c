@@ -1,5 +1,6 @@
 /*
- * vdf_oracle.c -- CPU oracle for the directional vector filters (BVDF, DDF).
+ * vdf_oracle.c -- CPU oracle for the directional vector filters (BVDF, DDF)
+ * and the vector median filter (VMF).
  *
  * TEST INFRASTRUCTURE ONLY.  This file is the slow, plain reference that the
  * CUDA path is checked against.  Only the tests, the package's smoke check and
@@ -18,6 +19,10 @@
  *   - Eq. (3), DDF: argmin_i (sum_j A)^p * (sum_j L2)^(1-p), with L2 the
  *     Minkowski distance of Eq. (1) at order 2 (Section III).  p = 1/2 orders
  *     candidates exactly like Eq. (3)'s plain product.
+ *   - Eq. (1), VMF: argmin_i sum_j L(x_i, x_j), L the Minkowski distance
+ *     (sum_k |x_k - y_k|^o)^(1/o).  Orders o = 1 and 2, and the limit
+ *     o -> infinity, max_k |x_k - y_k|; the same orders may replace L2 inside
+ *     the DDF.  Section III uses order 2 throughout.
  *   - Method 1 (Section 2.1, Eqs. (4)-(6), Table 1): A replaced by the
  *     degree-q minimax polynomial of Table 1: P_ACOS(z) for z < 0.5 and
  *     P_ASIN(tau) with tau = sqrt(1 - z) for z >= 0.5.
@@ -61,7 +66,9 @@
 
 typedef _Float128 q128;
 
-enum { O_BVDF = 0, O_DDF = 1 };
+enum { O_BVDF = 0, O_DDF = 1, O_VMF = 2 };
+/* Minkowski order of Eq. (1): 1, 2, or 0 for the limit of infinite order. */
+enum { O_LINF = 0, O_L1 = 1, O_L2 = 2 };
 enum { O_EXACT = 0, O_MINIMAX = 1, O_RGB = 2 };
 
 /* Flags written per pixel. */
@@ -252,6 +259,33 @@ static q128 l2_q(const double *x, const double *y)
     return sqrtf128(e);
 }
 
+/* Eq. (1) at order 1, 2 or infinity (the maximum of the component
+ * differences, the limit of the order-o distance as o grows). */
+static double lterm_d(const double *x, const double *y, int lp)
+{
+    if (lp == O_L2) return l2_d(x, y);
+    double s = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        const double a = fabs(x[k] - y[k]);
+        if (lp == O_L1) s += a;
+        else if (a > s) s = a;
+    }
+    return s;
+}
+
+static q128 lterm_q(const double *x, const double *y, int lp)
+{
+    if (lp == O_L2) return l2_q(x, y);
+    q128 s = 0;
+    for (int k = 0; k < 3; ++k) {
+        q128 a = (q128)x[k] - y[k];
+        if (a < 0) a = -a;
+        if (lp == O_L1) s += a;
+        else if (a > s) s = a;
+    }
+    return s;
+}
+
 /* Angular term of the chosen distance mode (the value summed into the first
  * aggregate).  For DDF with Method 2 the chromaticity distance goes through
  * Eq. (10) first. */
@@ -284,6 +318,7 @@ static q128 aterm_q(const double *x, const double *y, int filter, int dist, int 
 typedef struct {
     int filter, dist, q;
     double p;
+    int lp;   /* Minkowski order of the distance term (DDF, VMF) */
 } cfg_t;
 
 /* Scores of all n members in double.  sa/sl receive the aggregates. */
@@ -292,12 +327,13 @@ static void scores_d(const double *v, int n, const cfg_t *c, double *score, doub
     for (int i = 0; i < n; ++i) {
         double a = 0.0, l = 0.0;
         for (int j = 0; j < n; ++j) {
-            a += aterm_d(v + 3 * i, v + 3 * j, c->filter, c->dist, c->q);
-            if (c->filter == O_DDF) l += l2_d(v + 3 * i, v + 3 * j);
+            if (c->filter != O_VMF) a += aterm_d(v + 3 * i, v + 3 * j, c->filter, c->dist, c->q);
+            if (c->filter != O_BVDF) l += lterm_d(v + 3 * i, v + 3 * j, c->lp);
         }
         sa[i] = a;
         sl[i] = l;
         if (c->filter == O_BVDF) score[i] = a;
+        else if (c->filter == O_VMF) score[i] = l;
         else score[i] = pow(a > 0.0 ? a : 0.0, c->p) * pow(l, 1.0 - c->p);
     }
 }
@@ -307,12 +343,13 @@ static q128 score_q(const double *v, int n, int i, const cfg_t *c, q128 *sa, q12
 {
     q128 a = 0, l = 0;
     for (int j = 0; j < n; ++j) {
-        a += aterm_q(v + 3 * i, v + 3 * j, c->filter, c->dist, c->q);
-        if (c->filter == O_DDF) l += l2_q(v + 3 * i, v + 3 * j);
+        if (c->filter != O_VMF) a += aterm_q(v + 3 * i, v + 3 * j, c->filter, c->dist, c->q);
+        if (c->filter != O_BVDF) l += lterm_q(v + 3 * i, v + 3 * j, c->lp);
     }
     if (sa) *sa = a;
     if (sl) *sl = l;
     if (c->filter == O_BVDF) return a;
+    if (c->filter == O_VMF) return l;
     q128 pq = (q128)c->p;
     return powf128(a > 0 ? a : (q128)0, pq) * powf128(l, 1 - pq);
 }
@@ -322,7 +359,8 @@ static q128 score_q(const double *v, int n, int i, const cfg_t *c, q128 *sa, q12
 /* Select the output member of one window (vectors v, n of them, raster
  * order).  Returns the member index; *flags receives the O_FLAG_* bits.  If
  * agg is non-NULL it receives the binary128 aggregates rounded to double,
- * laid out as agg[2*i] = sum_j A, agg[2*i+1] = sum_j L2 (0 for BVDF). */
+ * laid out as agg[2*i] = sum_j A (0 for VMF), agg[2*i+1] = sum_j L (0 for
+ * BVDF). */
 static int select_window(const double *v, int n, const cfg_t *c, int *flags, double *agg)
 {
     double score[O_MAXN], sa[O_MAXN], sl[O_MAXN];
@@ -375,10 +413,11 @@ static int select_window(const double *v, int n, const cfg_t *c, int *flags, dou
 
 static int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
-static int check_cfg(int win, int filter, double p, int dist, int q)
+static int check_cfg(int win, int filter, double p, int dist, int q, int lp)
 {
     if (win < 1 || win > 7 || (win & 1) == 0) return -1;
-    if (filter != O_BVDF && filter != O_DDF) return -1;
+    if (filter != O_BVDF && filter != O_DDF && filter != O_VMF) return -1;
+    if (lp != O_L1 && lp != O_L2 && lp != O_LINF) return -1;
     if (dist < O_EXACT || dist > O_RGB) return -1;
     if (dist == O_MINIMAX && (q < 2 || q > 4)) return -1;
     if (filter == O_DDF && !(p >= 0.0 && p <= 1.0)) return -1;
@@ -392,14 +431,14 @@ static int check_cfg(int win, int filter, double p, int dist, int q)
  * (outputs have `count` entries).  out: 3 bytes per output pixel; idx: the
  * selected member's raster index; flags (optional): O_FLAG_* bits; agg
  * (optional): 2*n doubles per output pixel.  Returns 0 or -1 on bad input. */
-int vdf_oracle_filter_u8(const uint8_t *img, int M, int N, int win, int filter, double p, int dist, int q,
-                         const int64_t *pix, int64_t count, uint8_t *out, int8_t *idx, int32_t *flags,
-                         double *agg, int nthreads)
+int vdf_oracle_filter_u8_lp(const uint8_t *img, int M, int N, int win, int filter, double p, int lp, int dist,
+                            int q, const int64_t *pix, int64_t count, uint8_t *out, int8_t *idx, int32_t *flags,
+                            double *agg, int nthreads)
 {
-    if (!img || !out || M < 1 || N < 1 || check_cfg(win, filter, p, dist, q)) return -1;
+    if (!img || !out || M < 1 || N < 1 || check_cfg(win, filter, p, dist, q, lp)) return -1;
     init_consts();
     const int R = win / 2, n = win * win;
-    const cfg_t c = {filter, dist, q, p};
+    const cfg_t c = {filter, dist, q, p, lp};
     const int64_t total = pix ? count : (int64_t)M * N;
 #ifdef _OPENMP
     if (nthreads > 0) omp_set_num_threads(nthreads);
@@ -428,16 +467,25 @@ int vdf_oracle_filter_u8(const uint8_t *img, int M, int N, int win, int filter, 
     return 0;
 }
 
+/* The same at Minkowski order 2. */
+int vdf_oracle_filter_u8(const uint8_t *img, int M, int N, int win, int filter, double p, int dist, int q,
+                         const int64_t *pix, int64_t count, uint8_t *out, int8_t *idx, int32_t *flags,
+                         double *agg, int nthreads)
+{
+    return vdf_oracle_filter_u8_lp(img, M, N, win, filter, p, O_L2, dist, q, pix, count, out, idx, flags, agg,
+                                   nthreads);
+}
+
 /* Filter a B x 3 x M x N float32 (NCHW) batch; same conventions, pixel ids
- * run over B*M*N. */
+ * run over B*M*N; Minkowski order 2. */
 int vdf_oracle_filter_f32(const float *img, int B, int M, int N, int win, int filter, double p, int dist, int q,
                           const int64_t *pix, int64_t count, float *out, int8_t *idx, int32_t *flags,
                           double *agg, int nthreads)
 {
-    if (!img || !out || B < 1 || M < 1 || N < 1 || check_cfg(win, filter, p, dist, q)) return -1;
+    if (!img || !out || B < 1 || M < 1 || N < 1 || check_cfg(win, filter, p, dist, q, O_L2)) return -1;
     init_consts();
     const int R = win / 2, n = win * win;
-    const cfg_t c = {filter, dist, q, p};
+    const cfg_t c = {filter, dist, q, p, O_L2};
     const int64_t plane = (int64_t)M * N;
     const int64_t total = pix ? count : (int64_t)B * plane;
 #ifdef _OPENMP
@@ -473,14 +521,14 @@ int vdf_oracle_filter_f32(const float *img, int B, int M, int N, int win, int fi
 /* One window given directly as n vectors (n an odd square, raster order).
  * Writes the double screening scores and binary128 aggregates (rounded) and
  * returns the selected index, or -1 on bad input. */
-int vdf_oracle_window(const double *v, int n, int filter, double p, int dist, int q,
-                      double *score, double *agg, int32_t *flags)
+int vdf_oracle_window_lp(const double *v, int n, int filter, double p, int lp, int dist, int q,
+                         double *score, double *agg, int32_t *flags)
 {
     int w = 1;
     while (w * w < n) ++w;
-    if (!v || w * w != n || check_cfg(w, filter, p, dist, q)) return -1;
+    if (!v || w * w != n || check_cfg(w, filter, p, dist, q, lp)) return -1;
     init_consts();
-    const cfg_t c = {filter, dist, q, p};
+    const cfg_t c = {filter, dist, q, p, lp};
     double sa[O_MAXN], sl[O_MAXN], sc[O_MAXN];
     scores_d(v, n, &c, sc, sa, sl);
     if (score) memcpy(score, sc, sizeof(double) * n);
@@ -490,18 +538,25 @@ int vdf_oracle_window(const double *v, int n, int filter, double p, int dist, in
     return sel;
 }
 
+int vdf_oracle_window(const double *v, int n, int filter, double p, int dist, int q,
+                      double *score, double *agg, int32_t *flags)
+{
+    return vdf_oracle_window_lp(v, n, filter, p, O_L2, dist, q, score, agg, flags);
+}
+
 /* One pair term for the pins.  which: 0 = angular term of `dist` (BVDF
- * form), 1 = L2.  The double screening value goes to *d; the binary128 value
- * is returned split as *hi + *lo. */
+ * form), 1 = L2, 2 = L1, 3 = L-infinity.  The double screening value goes to
+ * *d; the binary128 value is returned split as *hi + *lo. */
 int vdf_oracle_term(const double *x, const double *y, int which, int dist, int q,
                     double *d, double *hi, double *lo)
 {
     if (!x || !y || dist < O_EXACT || dist > O_RGB || (dist == O_MINIMAX && (q < 2 || q > 4))) return -1;
     init_consts();
     q128 t;
-    if (which == 1) {
-        if (d) *d = l2_d(x, y);
-        t = l2_q(x, y);
+    if (which >= 1 && which <= 3) {
+        const int lp = which == 1 ? O_L2 : (which == 2 ? O_L1 : O_LINF);
+        if (d) *d = lterm_d(x, y, lp);
+        t = lterm_q(x, y, lp);
     } else {
         if (d) *d = aterm_d(x, y, O_BVDF, dist, q);
         t = aterm_q(x, y, O_BVDF, dist, q);

@@ -389,3 +389,111 @@ def test_filter_removes_impulses():
         for dist in ("exact", "minimax", "rgb"):
             y = oracle.filter_u8(noisy, 3, filter, 0.25, dist, 4)["out"]
             assert psnr(y, clean) > psnr(noisy, clean) + 8.0
+
+
+# ------------------------------------------ VMF and Minkowski orders (Eq. (1))
+
+ORDER_METRIC = {1: "cityblock", 2: "euclidean", "inf": "chebyshev"}
+
+
+@pytest.mark.parametrize("order", [1, 2, "inf"])
+def test_minkowski_terms_match_scipy(orc, order):
+    """Eq. (1) at orders 1, 2 and infinity against scipy's distances."""
+    rng = np.random.default_rng(21)
+    which = {1: "l1", 2: "l2", "inf": "linf"}[order]
+    for _ in range(300):
+        x, y = rng.integers(0, 256, 3).astype(float), rng.integers(0, 256, 3).astype(float)
+        ref = cdist(x[None], y[None], ORDER_METRIC[order])[0, 0]
+        d, hi, lo = orc.term(x, y, which)
+        assert abs(d - ref) <= 1e-15 * ref and abs((hi + lo) - ref) <= 1e-15 * ref
+
+
+def tie_rule_pick(minimisers, n):
+    """Centre if it is a minimiser, else the lowest index."""
+    centre = (n - 1) // 2
+    return centre if centre in minimisers else min(minimisers)
+
+
+@pytest.mark.parametrize("order", [1, 2, "inf"])
+@pytest.mark.parametrize("n", [9, 25])
+def test_vmf_window_brute_force(orc, order, n):
+    """Eq. (1) VMF: argmin of the summed scipy distances, ties by the tie rule
+    (integer vectors: the order-1 and infinity sums are exact integers)."""
+    rng = np.random.default_rng(22 + n)
+    for trial in range(150):
+        hi = 256 if trial % 3 else 4   # small ranges make exact ties common
+        v = rng.integers(0, hi, (n, 3)).astype(float)
+        s = cdist(v, v, ORDER_METRIC[order]).sum(1)
+        if order == 2:
+            mins = np.flatnonzero(s <= s.min() * (1 + 1e-12))
+            if len(mins) > 1 and not all(np.array_equal(np.sort(cdist(v[[i]], v)[0]), np.sort(cdist(v[[mins[0]]], v)[0]))
+                                         for i in mins):
+                continue   # near-equal L2 sums that are not equal multisets: left to the binary128 stage
+        else:
+            mins = np.flatnonzero(s == s.min())
+        sel = orc.window(v, "vmf", order=order)[0]
+        assert sel == tie_rule_pick(list(mins), n)
+
+
+def gray_median_reference(img1, win):
+    """Textbook median filter of a single-channel image (edge replication),
+    returning, per pixel, the index the tie rule picks among the window
+    members equal to the median."""
+    R = win // 2
+    pad = np.pad(img1, R, mode="edge")
+    wins = sliding_window_view(pad, (win, win)).reshape(img1.shape + (win * win,))
+    med = np.median(wins, axis=-1)
+    eq = wins == med[..., None]
+    centre = (win * win - 1) // 2
+    first = np.argmax(eq, axis=-1)
+    return np.where(eq[..., centre], centre, first)
+
+
+@pytest.mark.parametrize("order", [1, 2, "inf"])
+@pytest.mark.parametrize("win", [3, 5])
+@pytest.mark.parametrize("channel", [None, 0, 1, 2])
+def test_vmf_reduces_to_the_median_filter(orc, order, win, channel):
+    """When the vectors differ along one direction only (gray pixels r = g = b,
+    or a single varying channel), every Minkowski distance is a fixed multiple
+    of the scalar difference, and the VMF of Eq. (1) is the scalar median
+    filter (numpy's median of each window, odd n)."""
+    rng = np.random.default_rng(23 + win)
+    M, N = 23, 31
+    s = rng.integers(0, 256, (M, N))
+    s[rng.random((M, N)) < 0.3] = 77   # repeated values: ties on the median
+    if channel is None:
+        img = np.repeat(s[..., None], 3, axis=2).astype(np.uint8)
+    else:
+        img = np.tile(rng.integers(0, 256, 3), (M, N, 1)).astype(np.uint8)
+        img[..., channel] = s
+    res = orc.filter_u8(img, win, "vmf", order=order)
+    assert np.array_equal(res["idx"], gray_median_reference(s, win))
+    assert np.array_equal(res["out"][..., 0 if channel is None else channel],
+                          np.median(sliding_window_view(np.pad(s, win // 2, mode="edge"), (win, win)),
+                                    axis=(-2, -1)).astype(np.uint8))
+
+
+@pytest.mark.parametrize("order", [1, "inf"])
+def test_ddf_order_limits(orc, order):
+    """Eq. (3) with the order-o distance: p = 0 gives the order-o VMF, p = 1
+    gives BVDF (the distance drops out)."""
+    rng = np.random.default_rng(24)
+    for _ in range(80):
+        v = rng.integers(0, 256, (25, 3)).astype(float)
+        assert orc.window(v, "ddf", 0.0, order=order)[0] == orc.window(v, "vmf", order=order)[0]
+        assert orc.window(v, "ddf", 1.0, order=order)[0] == orc.window(v, "bvdf", 0.5)[0]
+
+
+@pytest.mark.parametrize("order", [1, 2, "inf"])
+def test_vmf_constant_window_and_aggregates(orc, order):
+    """A constant window returns its centre; the aggregates of a window are
+    the scipy distance sums (first column 0 for VMF)."""
+    for n in (9, 25):
+        v = np.tile([[37.0, 99.0, 180.0]], (n, 1))
+        sel, _, _, fl = orc.window(v, "vmf", order=order)
+        assert sel == (n - 1) // 2 and fl & orc.FLAG_TIE
+    rng = np.random.default_rng(25)
+    v = rng.integers(0, 256, (25, 3)).astype(float)
+    _, sc, agg, _ = orc.window(v, "vmf", order=order)
+    ref = cdist(v, v, ORDER_METRIC[order]).sum(1)
+    assert np.allclose(agg[:, 1], ref, rtol=1e-15) and np.all(agg[:, 0] == 0) and np.allclose(sc, ref, rtol=1e-15)
