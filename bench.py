@@ -69,11 +69,15 @@ def ops_per_pixel(win: int, filt: str) -> int:
     pair terms of 30 ops (DDF: angle + L2) or 24 (BVDF: angle); per
     aggregate component (2 for DDF) (2w-1) w (w-1) row-sum adds plus w^3
     accumulator adds; per member 15 score ops (DDF) or 2 (BVDF) and 6
-    selection ops.  ops_per_pixel(5, "ddf") == ALU_OPS_PER_PIXEL."""
+    selection ops.  ops_per_pixel(5, "ddf") == ALU_OPS_PER_PIXEL.  VMF (Eq. (1)):
+    6 ops per pair term (three component differences and their combination),
+    one aggregate component, 2 score ops per member."""
     U, n = ((2 * win - 1) ** 2 - 1) // 2, win * win
     sums = (2 * win - 1) * win * (win - 1) + win ** 3
     if filt == "ddf":
         return U * 30 + 2 * sums + n * 15 + n * 6
+    if filt == "vmf":
+        return U * 6 + sums + n * 2 + n * 6
     return U * 24 + sums + n * 2 + n * 6
 SMS, FP32_LANES_PER_SM = 152, 128
 
@@ -254,6 +258,70 @@ def batch_images(count: int, seed: int):
     return out
 
 
+def run_vmf_workload(args):
+    """The vector median filter of Eq. (1) (5x5) on the 1080p frames, at
+    Minkowski orders 2 (the paper's), 1 and infinity: the FP32 path (with its
+    FP64 recheck; none is needed at orders 1 and infinity, whose aggregates are
+    exact integers) against the plain FP64 path, one call per frame."""
+    import torch
+
+    from paper_1009_0958_gb300 import build as vbuild
+    from paper_1009_0958_gb300 import vdf
+    vbuild.build()
+    dev = torch.device("cuda", 0)
+    ins = [torch.from_numpy(f).to(dev) for f in frames(FRAMES)]
+    outs = [torch.empty_like(x) for x in ins]
+    idxs = [torch.empty((M, N), dtype=torch.int8, device=dev) for _ in ins]
+    wst = vdf.alloc_workspace(M, N, "fp32", dev)
+    stream = torch.cuda.current_stream(dev)
+    shape, _ = vdf.autotune(ins[0], WIN, "vmf", P, reps=5)
+    K = args.steps
+
+    def timed(order, prec, steps):
+        for s in range(args.warmup):
+            vdf.filter(ins[s % FRAMES], WIN, "vmf", precision=prec, out=outs[s % FRAMES], index=idxs[s % FRAMES],
+                       workspace=wst, order=order)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for s in range(steps):
+            vdf.filter(ins[s % FRAMES], WIN, "vmf", precision=prec, out=outs[s % FRAMES], index=idxs[s % FRAMES],
+                       workspace=wst, order=order)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) / steps
+
+    orders = {}
+    with ClockSampler(0) as clk:
+        for order in (2, 1, "inf"):
+            ms = timed(order, "fp32", K)
+            rechecked = vdf.workspace_stats(wst)[0]
+            ms64 = timed(order, "fp64", max(3, min(K, 20)))
+            orders[str(order)] = {"value": M * N / (ms * 1e-3) / 1e6, "ms_per_step": ms,
+                                  "fp64_value": M * N / (ms64 * 1e-3) / 1e6, "speedup_vs_fp64": ms64 / ms,
+                                  "rechecked_last_frame": rechecked}
+    head = orders["2"]
+    ops = ops_per_pixel(WIN, "vmf")
+    achieved = ops * M * N / (head["ms_per_step"] * 1e-3) / 1e12
+    peak = SMS * FP32_LANES_PER_SM * 2.070e9 / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "T FP32-pipe ops/s",
+                "frac": achieved / peak, "traffic": None,
+                "kernel": "vdf::tile_kernel<R=2,VMF,order 2,FP32> (the whole call: counter reset, tile kernel, "
+                          "recheck)", "ops_per_pixel": ops,
+                "peak_basis": "152 SMs x 128 FP32 lanes x 2070 MHz max SM clock"}
+    line = {"metric": "Mpix/s, 5x5 VMF (Eq. (1), Minkowski order 2) on 1080p RGB: FP32+FP64-tie path",
+            "value": head["value"], "unit": UNIT, "n_gpus": 1, "steps": K, "warmup": args.warmup,
+            "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": "VMF 5x5 on the 1920x1080 frames of the DDF workload (sinusoid field + 12 "
+                                   "rectangles, 10% impulses), 24 frames (149 MB) in rotation", "M": M, "N": N,
+                       "win": WIN, "tuned_shape": vdf.tile_shapes()[shape]},
+            "orders": orders, "fp64_path": {"value": head["fp64_value"], "unit": UNIT},
+            "speedup_vs_fp64": head["speedup_vs_fp64"], "gpu_launches": 2 * K, "roofline": roofline,
+            "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
 def run_batch_workload(args):
     """256 uneven images, mixed 3x3/5x5 BVDF/DDF, one persistent launch per
     batch replayed from a CUDA graph, tile shapes from the autotuner."""
@@ -398,7 +466,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=None)
-    ap.add_argument("--workload", default="ddf5_1080p", choices=["ddf5_1080p", "ddf5_4k", "batch", "autograd"])
+    ap.add_argument("--workload", default="ddf5_1080p",
+                    choices=["ddf5_1080p", "ddf5_4k", "batch", "autograd", "vmf5_1080p"])
     ap.add_argument("--shape", type=int, default=None, help="force this FP32 tile shape instead of autotuning")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -410,6 +479,8 @@ def main():
         return run_batch_workload(args)
     if args.workload == "autograd":
         return run_autograd_workload(args)
+    if args.workload == "vmf5_1080p":
+        return run_vmf_workload(args)
 
     import torch
     import torch.distributed as dist

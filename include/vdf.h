@@ -11,6 +11,11 @@
  *     A(x, y) = acos(<x,y> / (|x| |y|)).
  *   - DDF, Eq. (3): (sum_j A)^p * (sum_j L2)^(1-p), L2 the Minkowski distance
  *     of Eq. (1) at order 2; p = 1/2 orders like Eq. (3)'s plain product.
+ *   - VMF, Eq. (1): aggregated Minkowski distance sum_j L(x_i, x_j),
+ *     L(x, y) = (sum_k |x_k - y_k|^o)^(1/o).  vdf_filter_lp selects the order
+ *     o in {1, 2} or the limit of infinite order (max_k |x_k - y_k|) for the
+ *     VMF and for the distance term of the DDF; every other entry point uses
+ *     order 2.
  *   - Method 1 (Section 2.1, Eqs. (4)-(6), Table 1): A replaced by a degree-q
  *     minimax polynomial.  Method 2 (Section 2.2, Eq. (7)): A replaced by the
  *     chromaticity distance B; inside DDF B goes through Eq. (10) first.
@@ -41,7 +46,10 @@
 extern "C" {
 #endif
 
-typedef enum { VDF_BVDF = 0, VDF_DDF = 1 } vdf_filter_kind;
+typedef enum { VDF_BVDF = 0, VDF_DDF = 1, VDF_VMF = 2 } vdf_filter_kind;
+
+/* Minkowski order argument of vdf_filter_lp for the limit of infinite order. */
+#define VDF_MINKOWSKI_INF 0
 
 /* Distance used in place of A (Section II; Methods 1 and 2). */
 typedef enum { VDF_DIST_EXACT = 0, VDF_DIST_MINIMAX = 1, VDF_DIST_RGB = 2 } vdf_dist_mode;
@@ -86,8 +94,10 @@ size_t vdf_workspace_bytes(int M, int N, int precision);
  *              per pixel and member i, sum_j A_ij then sum_j L2_ij (the
  *              latter 0 for BVDF).  For Method 2 in DDF the first value is
  *              1.436437 * sum_j B_ij + 0.027664 * n (Eq. (10)).
- *   win        3 or 5.   filter: vdf_filter_kind.   p: DDF exponent, [0, 1].
- *   dist_mode  vdf_dist_mode.  minimax_q: 2, 3 or 4 (used for MINIMAX only).
+ *   win        3 or 5.   filter: vdf_filter_kind (VDF_VMF at order 2).
+ *              p: DDF exponent, [0, 1].
+ *   dist_mode  vdf_dist_mode (ignored for VDF_VMF).  minimax_q: 2, 3 or 4
+ *              (used for MINIMAX only).
  *   precision  vdf_precision.
  *   workspace  device, vdf_workspace_bytes(M, N, precision) bytes, 256-byte
  *              aligned (NULL allowed when that size is 0).  Its contents on
@@ -97,6 +107,21 @@ size_t vdf_workspace_bytes(int M, int N, int precision);
 int vdf_filter(const uint8_t *img, int M, int N, int win, int filter, double p, int dist_mode, int minimax_q,
                int precision, uint8_t *out, int8_t *index_out, double *agg_out, void *workspace,
                size_t workspace_bytes, void *stream);
+
+/*
+ * vdf_filter with the Minkowski order of the distance term of Eq. (1):
+ *   minkowski_order  1, 2, or VDF_MINKOWSKI_INF.  Used by VDF_VMF and
+ *              VDF_DDF (ignored for VDF_BVDF).
+ * VDF_VMF: p and dist_mode are ignored (the filter has no angular term); at
+ * orders 1 and infinity its aggregates are exact integers in both precisions
+ * and no pixel is rechecked.  VDF_DDF at order 1 or infinity needs
+ * VDF_DIST_EXACT (else VDF_E_UNSUPPORTED).  agg_out, when given, holds
+ * sum_j A (0 for the VMF) then sum_j L per member.  Other arguments and
+ * errors as for vdf_filter (VDF_E_INVALID for any other order).
+ */
+int vdf_filter_lp(const uint8_t *img, int M, int N, int win, int filter, double p, int minkowski_order,
+                  int dist_mode, int minimax_q, int precision, uint8_t *out, int8_t *index_out, double *agg_out,
+                  void *workspace, size_t workspace_bytes, void *stream);
 
 /*
  * The two stages of vdf_filter with VDF_PREC_FP32_RECHECK, for callers that
@@ -162,7 +187,8 @@ int vdf_filter_host_frames(const uint8_t *const *img_host, uint8_t *const *out_h
  * Float32 batch variant (the differentiable path).  img: device, B x 3 x M x N
  * float32 (NCHW, any non-negative values, e.g. RGB in [0, 1]); out: same
  * shape; index_out: device, B x M x N int8 (may be NULL, but the backward
- * pass needs it).  Only VDF_DIST_EXACT is supported for float input.  The
+ * pass needs it).  Only VDF_BVDF and VDF_DDF with VDF_DIST_EXACT are
+ * supported for float input (else VDF_E_UNSUPPORTED).  The
  * FP64 precision computes the pair terms from the float32 values exactly
  * promoted to double.  VDF_PREC_FP32_RECHECK computes them in FP32 on
  * exponent-normalised pixels with certified bounds (Kahan cross products)

@@ -30,7 +30,7 @@ bool valid_common(int M, int N, int win, int filter, double p, int dist, int q, 
 {
     if (M < 1 || N < 1 || (long long)M * N > (1LL << 31) - 1) return false;
     if (win != 3 && win != 5) return false;
-    if (filter != VDF_BVDF && filter != VDF_DDF) return false;
+    if (filter != VDF_BVDF && filter != VDF_DDF && filter != VDF_VMF) return false;
     if (filter == VDF_DDF && !(p >= 0.0 && p <= 1.0)) return false;
     if (dist < VDF_DIST_EXACT || dist > VDF_DIST_RGB) return false;
     if (dist == VDF_DIST_MINIMAX && (q < 2 || q > 4)) return false;
@@ -60,12 +60,33 @@ int num_sms()
 // Tile shape of the FP32 kernel per (window, filter, distance mode): shape 0
 // until vdf_autotune or vdf_set_tuned_shape records another.
 std::mutex g_tune_mutex;
-int g_tuned[2][2][3] = {};
+int g_tuned[2][3][3] = {};
 
 int tuned_shape(int win, int filter, int dist)
 {
     std::lock_guard<std::mutex> lock(g_tune_mutex);
     return g_tuned[win / 2 - 1][filter][dist];
+}
+
+// Kernel dispatch by filter kind and Minkowski order (internal code): the
+// VMF and the orders 1 / infinity have their own instantiation units.
+cudaError_t run_tile32(const vdf::TileParams &prm, int R, int filter, int dist, int norm, int shape, cudaStream_t st)
+{
+    if (filter == VDF_VMF || norm != vdf::NL2) return vdf::run_fp32_lp(prm, R, filter, norm, shape, st);
+    return vdf::run_fp32(prm, R, filter, dist, shape, st);
+}
+
+cudaError_t run_tile64(const vdf::TileParams &prm, int R, int filter, int dist, int norm, cudaStream_t st)
+{
+    if (filter == VDF_VMF || norm != vdf::NL2) return vdf::run_fp64_lp(prm, R, filter, norm, st);
+    return vdf::run_fp64(prm, R, filter, dist, false, st);
+}
+
+cudaError_t run_recheck_any(const vdf::RecheckParams &rp, int R, int filter, int dist, int norm, int blocks,
+                            cudaStream_t st)
+{
+    if (filter == VDF_VMF || norm != vdf::NL2) return vdf::run_recheck_lp(rp, R, filter, norm, blocks, st);
+    return vdf::run_recheck(rp, R, filter, dist, blocks, st);
 }
 
 }  // namespace
@@ -133,7 +154,7 @@ static vdf::TileParams tile_params(const uint8_t *img, int M, int N, double p, i
 
 static int fp32_pass_shape(const uint8_t *img, int M, int N, int win, int filter, double p, int dist_mode,
                            int minimax_q, uint8_t *out, int8_t *index_out, void *workspace, size_t workspace_bytes,
-                           int shape, void *stream)
+                           int shape, void *stream, int norm = vdf::NL2)
 {
     int rc = check_filter_args(img, M, N, win, filter, p, dist_mode, minimax_q, VDF_PREC_FP32_RECHECK, out,
                                index_out, nullptr, workspace, workspace_bytes);
@@ -141,21 +162,22 @@ static int fp32_pass_shape(const uint8_t *img, int M, int N, int win, int filter
     cudaStream_t st = (cudaStream_t)stream;
     const vdf::TileParams prm = tile_params(img, M, N, p, minimax_q, out, index_out, nullptr, workspace);
     cudaError_t e = cudaMemsetAsync(prm.recheck_ctr, 0, 2 * sizeof(unsigned), st);
-    if (e == cudaSuccess) e = vdf::run_fp32(prm, win / 2, filter, dist_mode, shape, st);
+    if (e == cudaSuccess) e = run_tile32(prm, win / 2, filter, dist_mode, norm, shape, st);
     return cuda_fail(e);
 }
 
-int vdf_fp32_pass(const uint8_t *img, int M, int N, int win, int filter, double p, int dist_mode, int minimax_q,
-                  uint8_t *out, int8_t *index_out, void *workspace, size_t workspace_bytes, void *stream)
+static int fp32_pass_norm(const uint8_t *img, int M, int N, int win, int filter, double p, int dist_mode,
+                          int minimax_q, uint8_t *out, int8_t *index_out, void *workspace, size_t workspace_bytes,
+                          void *stream, int norm)
 {
     if (!valid_common(M, N, win, filter, p, dist_mode, minimax_q, VDF_PREC_FP32_RECHECK)) return VDF_E_INVALID;
     return fp32_pass_shape(img, M, N, win, filter, p, dist_mode, minimax_q, out, index_out, workspace,
-                           workspace_bytes, tuned_shape(win, filter, dist_mode), stream);
+                           workspace_bytes, tuned_shape(win, filter, dist_mode), stream, norm);
 }
 
-int vdf_fp64_recheck(const uint8_t *img, int M, int N, int win, int filter, double p, int dist_mode,
-                     int minimax_q, uint8_t *out, int8_t *index_out, void *workspace, size_t workspace_bytes,
-                     void *stream)
+static int fp64_recheck_norm(const uint8_t *img, int M, int N, int win, int filter, double p, int dist_mode,
+                             int minimax_q, uint8_t *out, int8_t *index_out, void *workspace,
+                             size_t workspace_bytes, void *stream, int norm)
 {
     int rc = check_filter_args(img, M, N, win, filter, p, dist_mode, minimax_q, VDF_PREC_FP32_RECHECK, out,
                                index_out, nullptr, workspace, workspace_bytes);
@@ -171,25 +193,60 @@ int vdf_fp64_recheck(const uint8_t *img, int M, int N, int win, int filter, doub
     rp.N = N;
     rp.p = p;
     rp.q = minimax_q;
-    return cuda_fail(vdf::run_recheck(rp, win / 2, filter, dist_mode, num_sms() * 16, (cudaStream_t)stream));
+    return cuda_fail(run_recheck_any(rp, win / 2, filter, dist_mode, norm, num_sms() * 16, (cudaStream_t)stream));
+}
+
+int vdf_fp32_pass(const uint8_t *img, int M, int N, int win, int filter, double p, int dist_mode, int minimax_q,
+                  uint8_t *out, int8_t *index_out, void *workspace, size_t workspace_bytes, void *stream)
+{
+    if (filter == VDF_VMF) dist_mode = VDF_DIST_EXACT;
+    return fp32_pass_norm(img, M, N, win, filter, p, dist_mode, minimax_q, out, index_out, workspace,
+                          workspace_bytes, stream, vdf::NL2);
+}
+
+int vdf_fp64_recheck(const uint8_t *img, int M, int N, int win, int filter, double p, int dist_mode,
+                     int minimax_q, uint8_t *out, int8_t *index_out, void *workspace, size_t workspace_bytes,
+                     void *stream)
+{
+    if (filter == VDF_VMF) dist_mode = VDF_DIST_EXACT;
+    return fp64_recheck_norm(img, M, N, win, filter, p, dist_mode, minimax_q, out, index_out, workspace,
+                             workspace_bytes, stream, vdf::NL2);
+}
+
+int vdf_filter_lp(const uint8_t *img, int M, int N, int win, int filter, double p, int minkowski_order,
+                  int dist_mode, int minimax_q, int precision, uint8_t *out, int8_t *index_out, double *agg_out,
+                  void *workspace, size_t workspace_bytes, void *stream)
+{
+    int norm;
+    switch (minkowski_order) {
+    case 2: norm = vdf::NL2; break;
+    case 1: norm = vdf::NL1; break;
+    case VDF_MINKOWSKI_INF: norm = vdf::NLINF; break;
+    default: return VDF_E_INVALID;
+    }
+    if (filter == VDF_BVDF) norm = vdf::NL2;               // no distance term
+    if (filter == VDF_VMF) dist_mode = VDF_DIST_EXACT;     // no angular term
+    int rc = check_filter_args(img, M, N, win, filter, p, dist_mode, minimax_q, precision, out, index_out, agg_out,
+                               workspace, workspace_bytes);
+    if (rc != VDF_OK) return rc;
+    if (filter == VDF_DDF && norm != vdf::NL2 && dist_mode != VDF_DIST_EXACT) return VDF_E_UNSUPPORTED;
+    if (precision == VDF_PREC_FP64) {
+        const vdf::TileParams prm = tile_params(img, M, N, p, minimax_q, out, index_out, agg_out, nullptr);
+        return cuda_fail(run_tile64(prm, win / 2, filter, dist_mode, norm, (cudaStream_t)stream));
+    }
+    rc = fp32_pass_norm(img, M, N, win, filter, p, dist_mode, minimax_q, out, index_out, workspace, workspace_bytes,
+                        stream, norm);
+    if (rc != VDF_OK) return rc;
+    return fp64_recheck_norm(img, M, N, win, filter, p, dist_mode, minimax_q, out, index_out, workspace,
+                             workspace_bytes, stream, norm);
 }
 
 int vdf_filter(const uint8_t *img, int M, int N, int win, int filter, double p, int dist_mode, int minimax_q,
                int precision, uint8_t *out, int8_t *index_out, double *agg_out, void *workspace,
                size_t workspace_bytes, void *stream)
 {
-    int rc = check_filter_args(img, M, N, win, filter, p, dist_mode, minimax_q, precision, out, index_out, agg_out,
-                               workspace, workspace_bytes);
-    if (rc != VDF_OK) return rc;
-    if (precision == VDF_PREC_FP64) {
-        const vdf::TileParams prm = tile_params(img, M, N, p, minimax_q, out, index_out, agg_out, nullptr);
-        return cuda_fail(vdf::run_fp64(prm, win / 2, filter, dist_mode, false, (cudaStream_t)stream));
-    }
-    rc = vdf_fp32_pass(img, M, N, win, filter, p, dist_mode, minimax_q, out, index_out, workspace, workspace_bytes,
-                       stream);
-    if (rc != VDF_OK) return rc;
-    return vdf_fp64_recheck(img, M, N, win, filter, p, dist_mode, minimax_q, out, index_out, workspace,
-                            workspace_bytes, stream);
+    return vdf_filter_lp(img, M, N, win, filter, p, 2, dist_mode, minimax_q, precision, out, index_out, agg_out,
+                         workspace, workspace_bytes, stream);
 }
 
 int vdf_workspace_stats(const void *workspace, int64_t *rechecked, int32_t *overflow, void *stream)
@@ -247,7 +304,7 @@ int vdf_filter_f32(const float *img, int B, int M, int N, int win, int filter, d
     if ((long long)B * M * N > (1LL << 31) - 1) return VDF_E_INVALID;
     const size_t bytes = (size_t)B * M * N * 3 * sizeof(float);
     if (overlaps(img, bytes, out, bytes)) return VDF_E_INVALID;
-    if (dist_mode != VDF_DIST_EXACT) return VDF_E_UNSUPPORTED;
+    if (dist_mode != VDF_DIST_EXACT || filter == VDF_VMF) return VDF_E_UNSUPPORTED;
     if (index_out && (overlaps(index_out, (size_t)B * M * N, img, bytes) || overlaps(index_out, (size_t)B * M * N, out, bytes)))
         return VDF_E_INVALID;
     vdf::TileParams prm{};
@@ -309,14 +366,15 @@ int vdf_tile_shape(int shape, int *tile_w, int *tile_h)
 
 int vdf_get_tuned_shape(int win, int filter, int dist_mode)
 {
-    if ((win != 3 && win != 5) || filter < 0 || filter > 1 || dist_mode < 0 || dist_mode > 2) return VDF_E_INVALID;
-    return tuned_shape(win, filter, dist_mode);
+    if ((win != 3 && win != 5) || filter < 0 || filter > 2 || dist_mode < 0 || dist_mode > 2) return VDF_E_INVALID;
+    return tuned_shape(win, filter, filter == VDF_VMF ? VDF_DIST_EXACT : dist_mode);
 }
 
 int vdf_set_tuned_shape(int win, int filter, int dist_mode, int shape)
 {
-    if ((win != 3 && win != 5) || filter < 0 || filter > 1 || dist_mode < 0 || dist_mode > 2) return VDF_E_INVALID;
+    if ((win != 3 && win != 5) || filter < 0 || filter > 2 || dist_mode < 0 || dist_mode > 2) return VDF_E_INVALID;
     if (shape < 0 || shape >= vdf::kNumShapes32) return VDF_E_INVALID;
+    if (filter == VDF_VMF) dist_mode = VDF_DIST_EXACT;   // one entry: the VMF has no angular term
     std::lock_guard<std::mutex> lock(g_tune_mutex);
     g_tuned[win / 2 - 1][filter][dist_mode] = shape;
     return VDF_OK;
@@ -326,6 +384,7 @@ int vdf_autotune(const uint8_t *img, int M, int N, int win, int filter, double p
                  uint8_t *out, int8_t *index_out, void *workspace, size_t workspace_bytes, int reps, void *stream,
                  int *best_shape, float *best_ms)
 {
+    if (filter == VDF_VMF) dist_mode = VDF_DIST_EXACT;
     int rc = check_filter_args(img, M, N, win, filter, p, dist_mode, minimax_q, VDF_PREC_FP32_RECHECK, out,
                                index_out, nullptr, workspace, workspace_bytes);
     if (rc != VDF_OK) return rc;
@@ -376,6 +435,7 @@ int vdf_autotune(const uint8_t *img, int M, int N, int win, int filter, double p
 int vdf_debug_fp32_scores(const uint8_t *img, int M, int N, int win, int filter, double p, int dist_mode,
                           int minimax_q, float *fe_out, void *stream)
 {
+    if (filter == VDF_VMF) dist_mode = VDF_DIST_EXACT;
     if (!img || !fe_out || !valid_common(M, N, win, filter, p, dist_mode, minimax_q, VDF_PREC_FP32_RECHECK))
         return VDF_E_INVALID;
     vdf::TileParams prm{};
@@ -386,7 +446,7 @@ int vdf_debug_fp32_scores(const uint8_t *img, int M, int N, int win, int filter,
     prm.B = 1;
     prm.p = p;
     prm.q = minimax_q;
-    return cuda_fail(vdf::run_fp32(prm, win / 2, filter, dist_mode, 0, (cudaStream_t)stream));
+    return cuda_fail(run_tile32(prm, win / 2, filter, dist_mode, vdf::NL2, 0, (cudaStream_t)stream));
 }
 
 int vdf_debug_fp32_terms(const int *pairs, int n, int dist_mode, int minimax_q, float *angle_out, float *l2_out,

@@ -27,6 +27,12 @@ cudaError_t run_fp32_f32in(const TileParams &prm, int R, int filter, cudaStream_
 cudaError_t run_recheck(const RecheckParams &prm, int R, int filter, int dist, int blocks, cudaStream_t st,
                         bool f32in = false);
 
+// The VMF and the Minkowski orders 1 and infinity (uint8 input, exact
+// mode): filter VMF at norm NL2 / NL1 / NLINF, or DDF at NL1 / NLINF.
+cudaError_t run_fp32_lp(const TileParams &prm, int R, int filter, int norm, int shape, cudaStream_t st);
+cudaError_t run_fp64_lp(const TileParams &prm, int R, int filter, int norm, cudaStream_t st);
+cudaError_t run_recheck_lp(const RecheckParams &prm, int R, int filter, int norm, int blocks, cudaStream_t st);
+
 // FP32 pair terms of n pixel pairs (n x 6 ints), as the FP32 tile kernel computes them.
 cudaError_t run_debug_terms(const int *pairs, int n, int dist, int q, float *angle_out, float *l2_out,
                             cudaStream_t st);

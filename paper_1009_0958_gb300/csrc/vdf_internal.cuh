@@ -13,7 +13,10 @@
 
 namespace vdf {
 
-enum Filter { BVDF = 0, DDF = 1 };
+enum Filter { BVDF = 0, DDF = 1, VMF = 2 };
+// Minkowski order of the distance term of Eq. (1) (DDF, VMF): 2, 1, or the
+// limit of infinite order (the largest component difference).
+enum Norm { NL2 = 0, NL1 = 1, NLINF = 2 };
 enum Dist { EXACT = 0, MINIMAX = 1, RGB = 2 };
 
 // ------------------------------------------------------------- constants --
@@ -130,6 +133,20 @@ __device__ __forceinline__ double l2term64(const int4 a, const int4 b)
     return sqrt((double)(a.w + b.w - 2 * d));
 }
 
+// Eq. (1) at order 1 or in the limit of infinite order (the largest
+// component difference): exact integers.  Order 2 is l2term64.
+template <int NORM>
+__device__ __forceinline__ double lterm64(const int4 a, const int4 b)
+{
+    if constexpr (NORM == NL2) {
+        return l2term64(a, b);
+    } else {
+        const int e0 = abs(a.x - b.x), e1 = abs(a.y - b.y), e2 = abs(a.z - b.z);
+        if constexpr (NORM == NL1) return (double)(e0 + e1 + e2);
+        else return (double)max(e0, max(e1, e2));
+    }
+}
+
 // FP64 terms for float32 inputs (exact mode only): products of two float32
 // values are exact in double; each cross-product component is rounded once.
 __device__ __forceinline__ double aterm64f(const float4 a, const float4 b)
@@ -240,6 +257,20 @@ __device__ __forceinline__ float l2term32(const float4 a, const float4 b, float 
     float r;
     asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(e));
     return r;
+}
+
+// Eq. (1) in FP32 for integer-valued pixels: order 2 as l2term32 (d = <x,y>),
+// orders 1 and infinity exact (integer differences; sums below 2^24).
+template <int NORM>
+__device__ __forceinline__ float lterm32(const float4 a, const float4 b, float d)
+{
+    if constexpr (NORM == NL2) {
+        return l2term32(a, b, d);
+    } else {
+        const float e0 = fabsf(a.x - b.x), e1 = fabsf(a.y - b.y), e2 = fabsf(a.z - b.z);
+        if constexpr (NORM == NL1) return e0 + e1 + e2;
+        else return fmaxf(e0, fmaxf(e1, e2));
+    }
 }
 
 // ------------------------------------------ FP32 terms, float32 input ----

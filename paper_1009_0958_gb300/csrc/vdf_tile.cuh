@@ -48,10 +48,15 @@ struct TileParams {
     int q;
 };
 
-template <int R_, int FILTER_, int DIST_, bool FP64_, bool F32IN_, int TW_, int TH_>
+template <int R_, int FILTER_, int DIST_, bool FP64_, bool F32IN_, int TW_, int TH_, int NORM_ = NL2>
 struct TileCfg {
-    static constexpr int R = R_, FILTER = FILTER_, DIST = DIST_, TW = TW_, TH = TH_;
+    static constexpr int R = R_, FILTER = FILTER_, DIST = DIST_, TW = TW_, TH = TH_, NORM = NORM_;
     static constexpr bool FP64 = FP64_, F32IN = F32IN_;
+    static_assert(FILTER != VMF || DIST == EXACT, "VMF has no angular term");
+    static_assert(!F32IN || (FILTER != VMF && NORM == NL2), "float input: BVDF / DDF at order 2");
+    // VMF at order 1 or infinity: the aggregates are exact integers in both
+    // precisions, so equal scores are exact ties
+    static constexpr bool EXACT_SCORES = FILTER == VMF && NORM != NL2;
     static constexpr int W = 2 * R + 1, NW = W * W, CENTRE = (NW - 1) / 2;
     static constexpr int CW = TW + 2 * R, CH = TH + 2 * R, NC = CW * CH;
     static constexpr int NT = (NC + 31) / 32 * 32;
@@ -101,7 +106,7 @@ struct TileCfg {
 template <int FILTER>
 __device__ __forceinline__ double score64(double sa, double sl, double p)
 {
-    if (FILTER == BVDF) return sa;
+    if (FILTER != DDF) return sa;   // BVDF: sum of angles; VMF: sum of distances
     double f = 0.0;
     if (p > 0.0) f = __dmul_rn(p, log(sa > 0.0 ? sa : 0.0));
     if (p < 1.0) f = __dadd_rn(f, __dmul_rn(1.0 - p, log(sl)));
@@ -117,7 +122,7 @@ __device__ __forceinline__ int select64(F f)
     double m = f(0);
 #pragma unroll 1
     for (int k = 1; k < NW; ++k) m = fmin(m, f(k));
-    const double tol = (FILTER == BVDF) ? 1e-11 * fmax(fabs(m), 1e-3) : 1e-11;
+    const double tol = (FILTER != DDF) ? 1e-11 * fmax(fabs(m), 1e-3) : 1e-11;
     constexpr int c = (NW - 1) / 2;
     if (f(c) == m || f(c) - m <= tol) return c;
 #pragma unroll 1
@@ -155,12 +160,14 @@ __device__ __forceinline__ float pow4_erel(int a)
     return kSafety * (a * relA + (4 - a) * relL + 3.0f * kU);
 }
 
-template <int R, int FILTER, int DIST, bool F32IN = false>
+template <int R, int FILTER, int DIST, bool F32IN = false, int NORM = NL2>
 __device__ __forceinline__ float2 score32(float sa, float sl, float p, int quarter)
 {
     constexpr int NW = (2 * R + 1) * (2 * R + 1);
     constexpr float S = 4.0f * R;
     constexpr float kA = F32IN ? 24.0f : 16.0f, kL = F32IN ? 8.0f : 6.0f;   // term bounds, float / integer input
+    if (FILTER == VMF)   // sum of distances: order 2 as the L2 aggregate, orders 1 and infinity exact
+        return make_float2(sa, NORM == NL2 ? kSafety * (kL + S) * kU * sa : 0.0f);
     if (FILTER == BVDF) {
         float E;
         if (DIST == EXACT) E = (kA + S) * kU * sa;
@@ -240,17 +247,23 @@ __device__ __forceinline__ typename C::PlaneT pair_term(const typename C::Pix &a
                                                         const Aux &xa, const Aux &xb, int q)
 {
     typename C::PlaneT t;
-    if constexpr (C::FP64) {
+    if constexpr (C::FP64 && C::FILTER == VMF) {
+        t = lterm64<C::NORM>(a, b);   // Eq. (1)
+    } else if constexpr (C::FP64) {
         double ang, l2 = 0.0;
         if constexpr (C::F32IN) {
             ang = aterm64f(a, b);
             if constexpr (C::FILTER == DDF) l2 = l2term64f(a, b);
         } else {
             ang = aterm64<C::DIST>(a, b, q);
-            if constexpr (C::FILTER == DDF) l2 = l2term64(a, b);
+            if constexpr (C::FILTER == DDF) l2 = lterm64<C::NORM>(a, b);
         }
         if constexpr (C::FILTER == DDF) t = make_double2(ang, l2);
         else t = ang;
+    } else if constexpr (C::FILTER == VMF) {
+        float d = 0.0f;   // <x,y>, exact; order 2 only
+        if constexpr (C::NORM == NL2) d = fmaf(a.z, b.z, fmaf(a.y, b.y, a.x * b.x));
+        t = lterm32<C::NORM>(a, b, d);
     } else if constexpr (C::F32IN) {
         // float input, exact mode: normalised pixels (see normalize_f32)
         if constexpr (C::FILTER == DDF) t = make_float2(angle32f(a, b), l2term32f(a, b));
@@ -261,7 +274,7 @@ __device__ __forceinline__ typename C::PlaneT pair_term(const typename C::Pix &a
         if constexpr (C::DIST == EXACT) ang = angle32(r);
         else if constexpr (C::DIST == MINIMAX) ang = minimax32(r, xa, xb, q);
         else ang = chroma32(a, b, xa, xb);
-        if constexpr (C::FILTER == DDF) t = make_float2(ang, l2term32(a, b, r.d));
+        if constexpr (C::FILTER == DDF) t = make_float2(ang, lterm32<C::NORM>(a, b, r.d));
         else t = ang;
     }
     return t;
@@ -625,9 +638,10 @@ __device__ __forceinline__ void score_slots(const TileParams &prm, int b, int x0
             if constexpr (C::FILTER == DDF && C::DIST == RGB)
                 sa = __fma_rn(kSlope64, sa, (double)NW * kOffset64);   // Eq. (10) summed over j
             if (prm.agg) {
+                // sum_j A, sum_j L (VMF: 0, sum_j L)
                 double *ag = prm.agg + (((size_t)b * prm.M * prm.N + lin) * NW + k) * 2;
-                ag[0] = sa;
-                ag[1] = sl;
+                ag[0] = C::FILTER == VMF ? 0.0 : sa;
+                ag[1] = C::FILTER == VMF ? sa : sl;
             }
             const double sc = score64<C::FILTER>(sa, sl, prm.p);
             if constexpr (C::FILTER == DDF) hw[s].x = sc;
@@ -635,7 +649,7 @@ __device__ __forceinline__ void score_slots(const TileParams &prm, int b, int x0
         } else {
             float sa = hw[s].x;
             if constexpr (C::FILTER == DDF && C::DIST == RGB) sa = fmaf(kSlope32, sa, (float)NW * kOffset32);
-            const float2 v = score32<R, C::FILTER, C::DIST>(sa, hw[s].y, (float)prm.p, quarter);
+            const float2 v = score32<R, C::FILTER, C::DIST, false, C::NORM>(sa, hw[s].y, (float)prm.p, quarter);
             hw[s] = v;
             if (prm.dbg_fe) reinterpret_cast<float2 *>(prm.dbg_fe)[lin * NW + k] = v;
         }
@@ -718,6 +732,7 @@ __device__ __forceinline__ int resolve_near(unsigned near, const TileParams &prm
             }
         }
     }
+    if constexpr (C::EXACT_SCORES) equal = true;   // equal exact scores are ties
     if (!equal) {
         bool all_zero = true;
 #pragma unroll
@@ -774,12 +789,17 @@ __device__ __forceinline__ void select_and_store(const TileParams &prm, int b, i
         }
         // Relative bounds (BVDF with the exact or chromaticity terms, and DDF
         // with p = quarter / 4 scored by Omega^4): E = g * erel, g >= 0
-        bool relative = C::FILTER == BVDF && C::DIST != MINIMAX;
+        bool relative = (C::FILTER == BVDF && C::DIST != MINIMAX) || C::FILTER == VMF;
         if constexpr (C::FILTER == DDF && C::DIST != MINIMAX) relative = quarter >= 0;
         if (relative) {
             float g[NW];
             float erel;
-            if constexpr (C::FILTER == BVDF) {
+            if constexpr (C::FILTER == VMF) {
+#pragma unroll
+                for (int k = 0; k < NW; ++k) g[k] = f[k].x;
+                // order 2: the L2 aggregate's bound; orders 1, infinity: exact
+                erel = C::NORM == NL2 ? kSafety * (6.0f + 4.0f * R) * kU : 0.0f;
+            } else if constexpr (C::FILTER == BVDF) {
 #pragma unroll
                 for (int k = 0; k < NW; ++k) g[k] = f[k].x;
                 erel = kSafety * ((C::DIST == RGB ? 11.0f : (C::F32IN ? 24.0f : 16.0f)) + 4.0f * R) * kU;
@@ -817,7 +837,7 @@ __device__ __forceinline__ void select_and_store(const TileParams &prm, int b, i
                     // with floor 1e-3 for BVDF; in the log domain for DDF, a
                     // relative 4e-11 on Omega^4)
                     const float U = gmin * (1.0f + erel);
-                    const float delta = (C::FILTER == BVDF) ? 1e-9f * fmaxf(U, 1e-3f) + 1e-12f : 4e-9f * U;
+                    const float delta = (C::FILTER != DDF) ? 1e-9f * fmaxf(U, 1e-3f) + 1e-12f : 4e-9f * U;
                     const float thw = (U + delta) / (1.0f - erel) * up;
                     return unsure ? ALL : bit_mask<NW>([&](int k) { return g[k] <= thw; });
                 },
@@ -842,7 +862,7 @@ __device__ __forceinline__ void select_and_store(const TileParams &prm, int b, i
             for (int k = 0; k < NW; ++k) {
                 float sa = f[k].x;
                 if constexpr (C::FILTER == DDF && C::DIST == RGB) sa = fmaf(kSlope32, sa, (float)NW * kOffset32);
-                v[k] = score32<R, C::FILTER, C::DIST, C::F32IN>(sa, f[k].y, (float)prm.p, quarter);
+                v[k] = score32<R, C::FILTER, C::DIST, C::F32IN, C::NORM>(sa, f[k].y, (float)prm.p, quarter);
             }
             // U = min (f + E); the near set {f - E <= U} holds every true minimiser
             float hi[NW];
@@ -862,7 +882,7 @@ __device__ __forceinline__ void select_and_store(const TileParams &prm, int b, i
                     // widened by 100x the FP64 tie tolerance (1e-11: relative for
                     // BVDF, natural-log units for DDF, whose score here is Omega^4
                     // or log2 Omega)
-                    const float delta = (C::FILTER == BVDF) ? 1e-9f * fmaxf(fabsf(U), 1e-3f) + 1e-12f
+                    const float delta = (C::FILTER != DDF) ? 1e-9f * fmaxf(fabsf(U), 1e-3f) + 1e-12f
                                         : quarter >= 0   ? 4e-9f * fabsf(U)
                                                          : 1e-9f;
                     return unsure ? ALL : bit_mask<NW>([&](int k) { return v[k].x - v[k].y <= U + delta; });
@@ -1069,7 +1089,7 @@ struct RecheckCfg {
 // Recheck of one listed pixel by one warp.  `base` is the warp's shared
 // memory (RecheckCfg::PER_WARP bytes, 16-byte aligned).
 // F32IN: img and out are float32 B x 3 x M x N and lin = (b M + y) N + x.
-template <int R, int FILTER, int DIST, bool F32IN = false>
+template <int R, int FILTER, int DIST, bool F32IN = false, int NORM = NL2>
 __device__ __forceinline__ void recheck_pixel(const void *img, int M, int N, int lin, unsigned mask, void *out,
                                               int8_t *idx, double p, int q, unsigned char *base, int lane)
 {
@@ -1117,13 +1137,15 @@ __device__ __forceinline__ void recheck_pixel(const void *img, int M, int N, int
         unsigned row = ALL & ~(mask & ((1u << i) - 1u));
         for (int s = start; s < t; ++s) row &= row - 1;
         const int j = __ffs(row) - 1;
-        double a, l = 0.0;
+        double a, l = 0.0;   // VMF: a holds the distance term
         if constexpr (F32IN) {
             a = aterm64f(px[i], px[j]);
             if constexpr (FILTER == DDF) l = l2term64f(px[i], px[j]);
+        } else if constexpr (FILTER == VMF) {
+            a = lterm64<NORM>(px[i], px[j]);
         } else {
             a = aterm64<DIST>(px[i], px[j], q);
-            if constexpr (FILTER == DDF) l = l2term64(px[i], px[j]);
+            if constexpr (FILTER == DDF) l = lterm64<NORM>(px[i], px[j]);
         }
         Ma[i * NW + j] = a;
         if constexpr (FILTER == DDF) Ml[i * NW + j] = l;
@@ -1178,7 +1200,7 @@ __device__ __forceinline__ void recheck_pixel(const void *img, int M, int N, int
     __syncwarp();
 }
 
-template <int R, int FILTER, int DIST, bool F32IN>
+template <int R, int FILTER, int DIST, bool F32IN, int NORM>
 __global__ void __launch_bounds__(32) recheck_kernel(const RecheckParams prm)
 {
     using C = RecheckCfg<R, FILTER, DIST>;
@@ -1189,23 +1211,23 @@ __global__ void __launch_bounds__(32) recheck_kernel(const RecheckParams prm)
     const int nwarps = gridDim.x * C::WARPS;
     for (unsigned it = blockIdx.x * C::WARPS + wid; it < count; it += nwarps) {
         const int2 ent = prm.list[it];
-        recheck_pixel<R, FILTER, DIST, F32IN>(prm.img, prm.M, prm.N, ent.x, (unsigned)ent.y, prm.out, prm.idx, prm.p,
-                                              prm.q, base, lane);
+        recheck_pixel<R, FILTER, DIST, F32IN, NORM>(prm.img, prm.M, prm.N, ent.x, (unsigned)ent.y, prm.out, prm.idx,
+                                                    prm.p, prm.q, base, lane);
     }
 }
 
-template <int R, int FILTER, int DIST, bool F32IN = false>
+template <int R, int FILTER, int DIST, bool F32IN = false, int NORM = NL2>
 cudaError_t launch_recheck(const RecheckParams &prm, int blocks, cudaStream_t st)
 {
     using C = RecheckCfg<R, FILTER, DIST>;
     static bool configured = false;
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(recheck_kernel<R, FILTER, DIST, F32IN>,
+        cudaError_t e = cudaFuncSetAttribute(recheck_kernel<R, FILTER, DIST, F32IN, NORM>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    recheck_kernel<R, FILTER, DIST, F32IN><<<blocks, 32 * C::WARPS, C::SMEM, st>>>(prm);
+    recheck_kernel<R, FILTER, DIST, F32IN, NORM><<<blocks, 32 * C::WARPS, C::SMEM, st>>>(prm);
     return cudaGetLastError();
 }
 

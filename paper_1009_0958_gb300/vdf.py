@@ -15,7 +15,9 @@ import torch
 
 from . import build as _build
 
-FILTERS = {"bvdf": 0, "ddf": 1}
+FILTERS = {"bvdf": 0, "ddf": 1, "vmf": 2}
+# Minkowski order of the distance term (Eq. (1)): 1, 2, or "inf"
+ORDERS = {1: 1, 2: 2, "inf": 0}
 DISTS = {"exact": 0, "minimax": 1, "rgb": 2}
 PRECISIONS = {"fp64": 0, "fp32": 1}
 
@@ -41,6 +43,7 @@ def lib():
             L.vdf_workspace_bytes.argtypes, L.vdf_workspace_bytes.restype = [i, i, i], sz
             L.vdf_host_buffer_bytes.argtypes, L.vdf_host_buffer_bytes.restype = [i, i, i], sz
             L.vdf_filter.argtypes = [P, i, i, i, i, d, i, i, i, P, P, P, P, sz, P]
+            L.vdf_filter_lp.argtypes = [P, i, i, i, i, d, i, i, i, i, P, P, P, P, sz, P]
             L.vdf_filter_host.argtypes = [P, i, i, i, i, d, i, i, i, P, P, P, sz, P]
             L.vdf_filter_f32.argtypes = [P, i, i, i, i, i, d, i, i, i, P, P, P, sz, P]
             L.vdf_backward_f32.argtypes = [P, P, i, i, i, i, P, P]
@@ -53,7 +56,7 @@ def lib():
             L.vdf_debug_sqrt_error.argtypes = [P, P]
             L.vdf_host_frames_buffer_bytes.argtypes, L.vdf_host_frames_buffer_bytes.restype = [i, i, i], sz
             L.vdf_filter_host_frames.argtypes = [P, P, P, i, i, i, i, i, d, i, i, i, P, sz, P]
-            for f in ("vdf_filter", "vdf_filter_host", "vdf_workspace_stats", "vdf_debug_fp32_scores",
+            for f in ("vdf_filter", "vdf_filter_lp", "vdf_filter_host", "vdf_workspace_stats", "vdf_debug_fp32_scores",
                       "vdf_debug_fp32_terms", "vdf_filter_host_frames", "vdf_debug_fp32_terms_f32",
                       "vdf_debug_sqrt_error",
                       "vdf_fp32_pass", "vdf_fp64_recheck", "vdf_filter_f32", "vdf_backward_f32"):
@@ -106,8 +109,11 @@ def _aligned(ws: torch.Tensor | None):
 def filter(img: torch.Tensor, win: int = 3, filter="bvdf", p: float = 0.5, dist="exact", q: int = 4,
            precision="fp32", out: torch.Tensor | None = None, index: torch.Tensor | None = None,
            want_index: bool = True, agg: torch.Tensor | None = None, workspace: torch.Tensor | None = None,
-           stream=None):
-    """Filter an M x N x 3 uint8 CUDA image.  Returns ``(out, index)``."""
+           stream=None, order=2):
+    """Filter an M x N x 3 uint8 CUDA image.  Returns ``(out, index)``.
+
+    ``filter``: "bvdf", "ddf" or "vmf"; ``order``: Minkowski order of the
+    distance term of the DDF and the VMF (1, 2 or "inf")."""
     if not (img.is_cuda and img.dtype == torch.uint8 and img.dim() == 3 and img.shape[2] == 3):
         raise VdfError("img must be a CUDA uint8 tensor of shape (M, N, 3)")
     img = img.contiguous()
@@ -120,8 +126,11 @@ def filter(img: torch.Tensor, win: int = 3, filter="bvdf", p: float = 0.5, dist=
     if workspace is None:
         workspace = alloc_workspace(M, N, prec, img.device)
     wp, wn = _aligned(workspace)
-    _check(lib().vdf_filter(_ptr(img), M, N, win, _code(FILTERS, filter), float(p), _code(DISTS, dist), q, prec,
-                            _ptr(out), _ptr(index), _ptr(agg), wp, wn, _stream(stream)))
+    if order not in ORDERS:
+        raise VdfError("order must be 1, 2 or 'inf'")
+    _check(lib().vdf_filter_lp(_ptr(img), M, N, win, _code(FILTERS, filter), float(p), ORDERS[order],
+                               _code(DISTS, dist), q, prec, _ptr(out), _ptr(index), _ptr(agg), wp, wn,
+                               _stream(stream)))
     return out, index
 
 

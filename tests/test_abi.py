@@ -39,7 +39,8 @@ def test_strerror_and_sizes(L):
 
 
 @pytest.mark.parametrize("args", [
-    dict(img=None), dict(M=0), dict(N=-1), dict(win=4), dict(win=7), dict(filter=2), dict(filter=1, p=1.5), dict(filter=1, p=-0.1),
+    dict(img=None), dict(M=0), dict(N=-1), dict(win=4), dict(win=7), dict(filter=3), dict(filter=-1),
+    dict(filter=1, p=1.5), dict(filter=1, p=-0.1),
     dict(dist=3), dict(dist=1, q=5), dict(precision=2),
 ])
 def test_invalid_arguments_rejected_on_host(L, args):
@@ -49,6 +50,24 @@ def test_invalid_arguments_rejected_on_host(L, args):
     rc = L.vdf_filter(a["img"], a["M"], a["N"], a["win"], a["filter"], a["p"], a["dist"], a["q"], a["precision"],
                       a["out"], None, None, None, 0, None)
     assert rc == -1
+
+
+def test_minkowski_order_checked_on_host(L):
+    """vdf_filter_lp: orders 1, 2 and infinity (0) only; the DDF at order 1 or
+    infinity needs the exact angle; the VMF ignores p and dist_mode."""
+    img, out = ctypes.c_void_p(0x10000), ctypes.c_void_p(0x20000)
+
+    def call(filter, p, order, dist, precision=0, M=8):
+        return L.vdf_filter_lp(img, M, 8, 3, filter, p, order, dist, 4, precision, out, None, None, None, 0, None)
+    for order in (3, -1, 4):
+        assert call(2, 0.5, order, 0) == -1
+    assert call(1, 0.25, 1, 2) == -6                     # DDF, order 1, Method 2
+    assert call(1, 0.25, 0, 1) == -6                     # DDF, order infinity, Method 1
+    assert call(2, 0.25, 1, 0, M=0) == -1                # sizes still checked
+    assert call(2, 7.0, 1, 0, precision=1) == -5         # VMF: p ignored, reaches the workspace check
+    assert call(1, 7.0, 1, 0, precision=1) == -1         # DDF: p checked
+    f32 = L.vdf_filter_f32(img, 1, 8, 8, 3, 2, 0.5, 0, 4, 0, out, None, None, 0, None)
+    assert f32 == -6                                     # no VMF on the float path
 
 
 def test_aliasing_and_workspace_checks(L):
