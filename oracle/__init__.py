@@ -51,12 +51,16 @@ def lib():
             L.vdf_oracle_filter_u8.argtypes = [P, i, i, i, i, d, i, i, P, i64, P, P, P, P, i]
             L.vdf_oracle_filter_u8_lp.argtypes = [P, i, i, i, i, d, i, i, i, P, i64, P, P, P, P, i]
             L.vdf_oracle_window_lp.argtypes = [P, i, i, d, i, i, i, P, P, P]
+            L.vdf_oracle_filter_acwddf.argtypes = [P, i, i, i, i, i, i, d, P, i64, P, P, P, i]
+            L.vdf_oracle_window_acwddf.argtypes = [P, i, i, i, i, d, P, P, P]
+            L.vdf_oracle_window_cwvmf.argtypes = [P, i, i, P]
             L.vdf_oracle_filter_f32.argtypes = [P, i, i, i, i, i, d, i, i, P, i64, P, P, P, P, i]
             L.vdf_oracle_window.argtypes = [P, i, i, d, i, i, P, P, P]
             L.vdf_oracle_term.argtypes = [P, P, i, i, i, P, P, P]
             L.vdf_oracle_poly.argtypes = [i, i, d, P, P]
             L.vdf_oracle_max_threads.argtypes = []
             for f in ("vdf_oracle_filter_u8", "vdf_oracle_filter_u8_lp", "vdf_oracle_window_lp",
+                      "vdf_oracle_filter_acwddf", "vdf_oracle_window_acwddf", "vdf_oracle_window_cwvmf",
                       "vdf_oracle_filter_f32", "vdf_oracle_window",
                       "vdf_oracle_term", "vdf_oracle_poly", "vdf_oracle_max_threads"):
                 getattr(L, f).restype = ctypes.c_int
@@ -145,6 +149,52 @@ def window(vecs, filter="bvdf", p=0.5, dist="exact", q=4, order=2):
     if sel < 0:
         raise ValueError("oracle rejected the arguments")
     return sel, score, agg, int(fl[0])
+
+
+def filter_acwddf(img, win=3, dist="exact", q=4, lam=2, T=10.8, pixels=None, threads=0):
+    """ACWDDF (Eq. (9)) of an M x N x 3 uint8 image: dict with ``out``,
+    ``idx`` and ``flags`` as :func:`filter_u8`."""
+    img = np.ascontiguousarray(img, dtype=np.uint8)
+    M, N = img.shape[:2]
+    _, dm = _cfg(0, dist)
+    if pixels is None:
+        shape, count, pix = (M, N), M * N, None
+    else:
+        pix = np.ascontiguousarray(pixels, dtype=np.int64)
+        shape, count = (pix.shape[0],), pix.shape[0]
+    out = np.zeros(shape + (3,), np.uint8)
+    idx = np.zeros(shape, np.int8)
+    flags = np.zeros(shape, np.int32)
+    rc = lib().vdf_oracle_filter_acwddf(_ptr(img), M, N, win, dm, q, lam, float(T), _ptr(pix), count, _ptr(out),
+                                        _ptr(idx), _ptr(flags), threads)
+    if rc != 0:
+        raise ValueError("oracle rejected the arguments")
+    return {"out": out, "idx": idx, "flags": flags}
+
+
+def window_acwddf(vecs, dist="exact", q=4, lam=2, T=10.8):
+    """ACWDDF of one window (n x 3, raster order): ``(index, cwvmf_indices,
+    switching_sum, flags)``."""
+    v = np.ascontiguousarray(vecs, dtype=np.float64)
+    _, dm = _cfg(0, dist)
+    cw = np.zeros(3, np.int32)
+    sm = np.zeros(1)
+    fl = np.zeros(1, np.int32)
+    sel = lib().vdf_oracle_window_acwddf(_ptr(v), v.shape[0], dm, q, lam, float(T), _ptr(cw), _ptr(sm), _ptr(fl))
+    if sel < 0:
+        raise ValueError("oracle rejected the arguments")
+    return sel, [int(c) for c in cw], float(sm[0]), int(fl[0])
+
+
+def window_cwvmf(vecs, k):
+    """Centre-weighted VMF of Eq. (9) of one window at smoothing level k:
+    ``(index, flags)``."""
+    v = np.ascontiguousarray(vecs, dtype=np.float64)
+    fl = np.zeros(1, np.int32)
+    sel = lib().vdf_oracle_window_cwvmf(_ptr(v), v.shape[0], k, _ptr(fl))
+    if sel < 0:
+        raise ValueError("oracle rejected the arguments")
+    return sel, int(fl[0])
 
 
 def term(x, y, which="angle", dist="exact", q=4):

@@ -23,6 +23,16 @@
  *     (sum_k |x_k - y_k|^o)^(1/o).  Orders o = 1 and 2, and the limit
  *     o -> infinity, max_k |x_k - y_k|; the same orders may replace L2 inside
  *     the DDF.  Section III uses order 2 throughout.
+ *   - Eq. (9), ACWDDF (Section 3.2): the DDF output if
+ *     sum_{k=lambda}^{lambda+2} A(y_k, x_d) L2(y_k, x_d) > T, else the centre
+ *     x_d, where y_k is the centre-weighted VMF output at smoothing level k,
+ *     argmin_i sum_j w_j(k) L2(x_i, x_j) with w_d(k) = n - 2k + 2 and w_j = 1
+ *     otherwise.  Readings: Eq. (9) names the outputs of the switching test
+ *     CWDDF^k but defines CWVMF^k; the defined CWVMF^k are used.  The DDF
+ *     inside is Eq. (3)'s plain product (p = 1/2 here) with A of the distance
+ *     mode (Method 2 through Eq. (10), as the paper does for this filter);
+ *     k stays within [1, d] (d = (n+1)/2, 1-based), so lambda is in
+ *     [1, d - 2]; the test is strict (> T).
  *   - Method 1 (Section 2.1, Eqs. (4)-(6), Table 1): A replaced by the
  *     degree-q minimax polynomial of Table 1: P_ACOS(z) for z < 0.5 and
  *     P_ASIN(tau) with tau = sqrt(1 - z) for z >= 0.5.
@@ -321,6 +331,13 @@ typedef struct {
     int lp;   /* Minkowski order of the distance term (DDF, VMF) */
 } cfg_t;
 
+/* Minimum of n scores with the tie rule: screening in double, binary128
+ * re-evaluation (score_q(i, ctx)) of the candidates within 1e-8 of the double
+ * minimum, ties within 1e-24; *flags receives the O_FLAG_* bits. */
+typedef q128 (*score_q_fn)(int i, const void *ctx);
+
+static int decide_min(const double *score, int n, score_q_fn fq, const void *ctx, int *flags);
+
 /* Scores of all n members in double.  sa/sl receive the aggregates. */
 static void scores_d(const double *v, int n, const cfg_t *c, double *score, double *sa, double *sl)
 {
@@ -409,6 +426,92 @@ static int select_window(const double *v, int n, const cfg_t *c, int *flags, dou
     }
     if (nt > 1) *flags |= O_FLAG_TIE;
     return best;
+}
+
+static int decide_min(const double *score, int n, score_q_fn fq, const void *ctx, int *flags)
+{
+    const int centre = (n - 1) / 2;
+    double m = score[0];
+    for (int i = 1; i < n; ++i)
+        if (score[i] < m) m = score[i];
+    const double screen = 1e-8 * (fabs(m) + 1e-3);
+    int cand[O_MAXN], nc = 0;
+    for (int i = 0; i < n; ++i)
+        if (score[i] - m <= screen) cand[nc++] = i;
+    if (nc == 1) return cand[0];
+    *flags |= O_FLAG_ESCALATED;
+    q128 s[O_MAXN], mq = 0;
+    for (int k = 0; k < nc; ++k) {
+        s[k] = fq(cand[k], ctx);
+        if (k == 0 || s[k] < mq) mq = s[k];
+    }
+    q128 scale = (mq < 0 ? -mq : mq) + (q128)1e-3;
+    int best = -1, nt = 0;
+    for (int k = 0; k < nc; ++k) {
+        q128 gap = s[k] - mq;
+        if (gap <= (q128)1e-24 * scale) {
+            ++nt;
+            if (cand[k] == centre) best = centre;
+            else if (best < 0) best = cand[k];
+        } else if (gap <= (q128)1e-9 * scale) {
+            *flags |= O_FLAG_GRAY;
+        }
+    }
+    if (nt > 1) *flags |= O_FLAG_TIE;
+    return best;
+}
+
+/* ------------------------------------------------------- ACWDDF, Eq. (9) -- */
+
+typedef struct {
+    const double *v;
+    int n;
+    double wd;   /* weight of the centre member */
+} cw_ctx;
+
+static q128 cwvmf_q(int i, const void *p)
+{
+    const cw_ctx *c = (const cw_ctx *)p;
+    const int d = (c->n - 1) / 2;
+    q128 s = 0;
+    for (int j = 0; j < c->n; ++j) s += (j == d ? (q128)c->wd : (q128)1) * l2_q(c->v + 3 * i, c->v + 3 * j);
+    return s;
+}
+
+/* Centre-weighted VMF of Eq. (9) at smoothing level k (1-based, k <= d). */
+static int select_cwvmf(const double *v, int n, int k, int *flags)
+{
+    const int d = (n - 1) / 2;
+    const cw_ctx c = {v, n, (double)(n - 2 * k + 2)};
+    double score[O_MAXN];
+    for (int i = 0; i < n; ++i) {
+        double s = 0.0;
+        for (int j = 0; j < n; ++j) s += (j == d ? c.wd : 1.0) * l2_d(v + 3 * i, v + 3 * j);
+        score[i] = s;
+    }
+    return decide_min(score, n, cwvmf_q, &c, flags);
+}
+
+/* ACWDDF of one window: returns the member index; cw[3] (optional) receives
+ * the three CWVMF outputs, *sum (optional) the switching sum. */
+static int select_acwddf(const double *v, int n, int dist, int q, int lambda, double T, int *flags, int *cw,
+                         double *sum)
+{
+    const cfg_t ddf = {O_DDF, dist, q, 0.5, O_L2};
+    const int d = (n - 1) / 2;
+    int fl = 0;
+    const int sel = select_window(v, n, &ddf, &fl, NULL);
+    q128 sq = 0;
+    for (int k = lambda; k <= lambda + 2; ++k) {
+        const int y = select_cwvmf(v, n, k, &fl);
+        if (cw) cw[k - lambda] = y;
+        sq += aterm_q(v + 3 * y, v + 3 * d, O_DDF, dist, q) * l2_q(v + 3 * y, v + 3 * d);
+    }
+    const q128 gap = sq - (q128)T;
+    if ((gap < 0 ? -gap : gap) <= (q128)1e-9 * ((q128)fabs(T) + 1)) fl |= O_FLAG_GRAY;
+    if (sum) *sum = (double)sq;
+    *flags = fl;
+    return sq > (q128)T ? sel : d;
 }
 
 static int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
@@ -578,6 +681,79 @@ int vdf_oracle_poly(int branch, int q, double t, double *hi, double *lo)
     *hi = h;
     *lo = (double)(v - (q128)h);
     return 0;
+}
+
+/* ACWDDF (Eq. (9)) of an M x N uint8 image, pixel subset as
+ * vdf_oracle_filter_u8.  lambda in [1, d - 2] with d = (win*win + 1)/2. */
+int vdf_oracle_filter_acwddf(const uint8_t *img, int M, int N, int win, int dist, int q, int lambda, double T,
+                             const int64_t *pix, int64_t count, uint8_t *out, int8_t *idx, int32_t *flags,
+                             int nthreads)
+{
+    const int n = win * win, d1 = (n + 1) / 2;
+    if (!img || !out || M < 1 || N < 1 || check_cfg(win, O_DDF, 0.5, dist, q, O_L2)) return -1;
+    if (lambda < 1 || lambda > d1 - 2 || !isfinite(T)) return -1;
+    init_consts();
+    const int R = win / 2;
+    const int64_t total = pix ? count : (int64_t)M * N;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 64)
+#endif
+    for (int64_t t = 0; t < total; ++t) {
+        const int64_t lin = pix ? pix[t] : t;
+        const int r = (int)(lin / N), col = (int)(lin % N);
+        double v[3 * O_MAXN];
+        int i = 0;
+        for (int dy = -R; dy <= R; ++dy)
+            for (int dx = -R; dx <= R; ++dx, ++i) {
+                const uint8_t *px = img + 3 * ((int64_t)clampi(r + dy, 0, M - 1) * N + clampi(col + dx, 0, N - 1));
+                v[3 * i] = px[0];
+                v[3 * i + 1] = px[1];
+                v[3 * i + 2] = px[2];
+            }
+        int fl;
+        const int sel = select_acwddf(v, n, dist, q, lambda, T, &fl, NULL, NULL);
+        out[3 * t] = (uint8_t)v[3 * sel];
+        out[3 * t + 1] = (uint8_t)v[3 * sel + 1];
+        out[3 * t + 2] = (uint8_t)v[3 * sel + 2];
+        if (idx) idx[t] = (int8_t)sel;
+        if (flags) flags[t] = fl;
+    }
+    return 0;
+}
+
+/* ACWDDF of one window (n vectors, raster order), with its intermediate
+ * results: cw[3] the CWVMF outputs at k = lambda .. lambda + 2, *sum the
+ * switching sum, *flags the O_FLAG_* bits.  Returns the index or -1. */
+int vdf_oracle_window_acwddf(const double *v, int n, int dist, int q, int lambda, double T, int32_t *cw,
+                             double *sum, int32_t *flags)
+{
+    int w = 1;
+    while (w * w < n) ++w;
+    if (!v || w * w != n || check_cfg(w, O_DDF, 0.5, dist, q, O_L2)) return -1;
+    if (lambda < 1 || lambda > (n + 1) / 2 - 2 || !isfinite(T)) return -1;
+    init_consts();
+    int c3[3], fl;
+    double s;
+    const int sel = select_acwddf(v, n, dist, q, lambda, T, &fl, c3, &s);
+    if (cw)
+        for (int k = 0; k < 3; ++k) cw[k] = c3[k];
+    if (sum) *sum = s;
+    if (flags) *flags = fl;
+    return sel;
+}
+
+/* Centre-weighted VMF of one window at smoothing level k (1..d). */
+int vdf_oracle_window_cwvmf(const double *v, int n, int k, int32_t *flags)
+{
+    int w = 1;
+    while (w * w < n) ++w;
+    if (!v || w * w != n || (w & 1) == 0 || k < 1 || k > (n + 1) / 2) return -1;
+    init_consts();
+    int fl = 0;
+    const int sel = select_cwvmf(v, n, k, &fl);
+    if (flags) *flags = fl;
+    return sel;
 }
 
 int vdf_oracle_max_threads(void)

@@ -497,3 +497,103 @@ def test_vmf_constant_window_and_aggregates(orc, order):
     _, sc, agg, _ = orc.window(v, "vmf", order=order)
     ref = cdist(v, v, ORDER_METRIC[order]).sum(1)
     assert np.allclose(agg[:, 1], ref, rtol=1e-15) and np.all(agg[:, 0] == 0) and np.allclose(sc, ref, rtol=1e-15)
+
+
+# ------------------------------------------------------------ ACWDDF (Eq. (9))
+
+def test_acwddf_closed_forms(orc):
+    """Eight equal neighbours a around a centre b, 3x3, lambda = 2 (centre
+    weights 7, 5, 3): each CWVMF level picks a (weighted sum 7 L(a,b) for a
+    against 8 L(a,b) for b), so the switching sum is 3 A(a,b) L2(a,b).
+    Orthogonal a, b: 3 (pi/2) 10 sqrt(2) = 66.6 > 10.8, the DDF output (a,
+    lowest index 0).  Nearly parallel: 3 atan(1/10) = 0.30 < 10.8, the
+    centre."""
+    v = np.tile([[10.0, 0.0, 0.0]], (9, 1))
+    v[4] = [0.0, 10.0, 0.0]
+    sel, cw, s, _ = orc.window_acwddf(v)
+    assert cw == [0, 0, 0] and sel == 0
+    assert abs(s - 3 * (math.pi / 2) * math.hypot(10, 10)) < 1e-12
+    v[4] = [10.0, 1.0, 0.0]
+    sel, cw, s, _ = orc.window_acwddf(v)
+    assert cw == [0, 0, 0] and sel == 4
+    assert abs(s - 3 * math.atan2(1, 10) * 1.0) < 1e-14
+
+
+@pytest.mark.parametrize("n", [9, 25])
+def test_cwvmf_is_the_centre_weighted_median_on_gray_windows(orc, n):
+    """Gray vectors: the CWVMF of Eq. (9) is the centre-weighted median (the
+    median of the values with the centre repeated w_d = n - 2k + 2 times;
+    numpy), the tie rule choosing among the members with that value."""
+    rng = np.random.default_rng(31 + n)
+    d = (n - 1) // 2
+    for _ in range(60):
+        g = rng.integers(0, 40, n).astype(float)
+        v = np.repeat(g[:, None], 3, axis=1)
+        for k in range(1, d + 2):
+            wd = n - 2 * k + 2
+            med = np.median(np.concatenate([g, np.full(wd - 1, g[d])]))
+            members = list(np.flatnonzero(g == med))
+            sel, _ = orc.window_cwvmf(v, k)
+            assert sel == tie_rule_pick(members, n)
+
+
+@pytest.mark.parametrize("n", [9, 25])
+def test_cwvmf_brute_force_scipy(orc, n):
+    """Eq. (9)'s weighted sum of scipy Euclidean distances, every level k;
+    at k = d the weights are all 1 and the CWVMF is the order-2 VMF."""
+    rng = np.random.default_rng(33 + n)
+    d = (n - 1) // 2
+    for _ in range(40):
+        v = rng.integers(0, 256, (n, 3)).astype(float)
+        D = cdist(v, v)
+        for k in range(1, d + 2):
+            w = np.ones(n)
+            w[d] = n - 2 * k + 2
+            s = D @ w
+            assert orc.window_cwvmf(v, k)[0] == int(np.argmin(s))
+        assert orc.window_cwvmf(v, d + 1)[0] == orc.window(v, "vmf", order=2)[0]
+
+
+def test_acwddf_switching_sum_matches_scipy(orc):
+    """The switching sum is sum over the three levels of the angle (scipy
+    cosine distance -> arccos) times the Euclidean distance between the CWVMF
+    output and the centre; the output follows the test against T."""
+    rng = np.random.default_rng(35)
+    for n in (9, 25):
+        d = (n - 1) // 2
+        for _ in range(40):
+            v = rng.integers(1, 256, (n, 3)).astype(float)
+            v[d] = rng.integers(1, 256, 3)
+            for T in (10.8, 0.5, 200.0):
+                sel, cw, s, fl = orc.window_acwddf(v, T=T)
+                ref = 0.0
+                for y in cw:
+                    cosd = cdist(v[[y]], v[[d]], "cosine")[0, 0]
+                    ref += math.acos(min(1.0, max(-1.0, 1.0 - cosd))) * cdist(v[[y]], v[[d]])[0, 0]
+                assert abs(s - ref) <= 1e-7 * max(1.0, ref)
+                if not fl & orc.FLAG_GRAY:
+                    ddf = orc.window(v, "ddf", 0.5, "exact")[0]
+                    assert sel == (ddf if s > T else d)
+
+
+@pytest.mark.parametrize("win", [3, 5])
+@pytest.mark.parametrize("dist", ["exact", "minimax", "rgb"])
+def test_acwddf_threshold_limits(orc, win, dist):
+    """T above any attainable sum: the identity filter (the input image).  T
+    below 0: the DDF (Eq. (3), p = 1/2) everywhere."""
+    from paper_1009_0958_gb300 import synth
+    _, img = synth.make_image(19, 23, 37, 0.2, rectangles=3)
+    hi = orc.filter_acwddf(img, win, dist, T=1e30)
+    assert np.array_equal(hi["out"], img) and np.all(hi["idx"] == (win * win - 1) // 2)
+    lo = orc.filter_acwddf(img, win, dist, T=-1.0)
+    ddf = orc.filter_u8(img, win, "ddf", 0.5, dist)
+    assert np.array_equal(lo["idx"], ddf["idx"]) and np.array_equal(lo["out"], ddf["out"])
+
+
+def test_acwddf_rejects_bad_levels(orc):
+    v = np.zeros((9, 3))
+    with pytest.raises(ValueError):
+        orc.window_acwddf(v, lam=0)
+    with pytest.raises(ValueError):
+        orc.window_acwddf(v, lam=4)     # 3x3: k would exceed d = 5
+    orc.window_acwddf(v, lam=3)
