@@ -322,6 +322,73 @@ def run_vmf_workload(args):
     print(json.dumps(line), flush=True)
 
 
+def run_acwddf_workload(args):
+    """The ACWDDF of Eq. (9) (Section 3.2, lambda = 2, T = 10.8) on the 1080p
+    frames: 3x3 (the paper's window) in the three distance modes, and 5x5
+    exact; the FP32 certified path (whole-pixel FP64 recheck where a decision
+    is open) against the plain FP64 path, one call per frame."""
+    import torch
+
+    from paper_1009_0958_gb300 import build as vbuild
+    from paper_1009_0958_gb300 import vdf
+    vbuild.build()
+    dev = torch.device("cuda", 0)
+    ins = [torch.from_numpy(f).to(dev) for f in frames(FRAMES)]
+    outs = [torch.empty_like(x) for x in ins]
+    idxs = [torch.empty((M, N), dtype=torch.int8, device=dev) for _ in ins]
+    wst = vdf.alloc_workspace(M, N, "fp32", dev)
+    stream = torch.cuda.current_stream(dev)
+    K = args.steps
+    for win in (3, 5):
+        for dist in ("exact", "minimax", "rgb"):
+            vdf.autotune(ins[0], win, "ddf", 0.5, dist, reps=3)
+
+    def timed(win, dist, prec, steps):
+        def call(s):
+            vdf.filter_acwddf(ins[s % FRAMES], win, dist, 4, 2, 10.8, precision=prec, out=outs[s % FRAMES],
+                              index=idxs[s % FRAMES], workspace=wst)
+        for s in range(args.warmup):
+            call(s)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for s in range(steps):
+            call(s)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) / steps
+
+    cases = {}
+    with ClockSampler(0) as clk:
+        for win, dist in ((3, "exact"), (3, "minimax"), (3, "rgb"), (5, "exact")):
+            ms = timed(win, dist, "fp32", K)
+            rechecked = vdf.workspace_stats(wst)[0]
+            ms64 = timed(win, dist, "fp64", max(3, min(K, 10)))
+            cases[f"{win}x{win} {dist}"] = {"value": M * N / (ms * 1e-3) / 1e6, "ms_per_step": ms,
+                                            "fp64_value": M * N / (ms64 * 1e-3) / 1e6,
+                                            "speedup_vs_fp64": ms64 / ms, "rechecked_last_frame": rechecked}
+    head = cases["3x3 exact"]
+    ops = ops_per_pixel(3, "ddf")
+    achieved = ops * M * N / (head["ms_per_step"] * 1e-3) / 1e12
+    peak = SMS * FP32_LANES_PER_SM * 2.070e9 / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "T FP32-pipe ops/s",
+                "frac": achieved / peak, "traffic": None,
+                "kernel": "vdf::tile_kernel<R=1,DDF,EXACT,FP32,ACW> (the whole call: counter reset, tile kernel, "
+                          "recheck); ops of the DDF only (the CWVMF levels and the switch not counted)",
+                "ops_per_pixel": ops, "peak_basis": "152 SMs x 128 FP32 lanes x 2070 MHz max SM clock"}
+    line = {"metric": "Mpix/s, 3x3 ACWDDF (Eq. (9), lambda 2, T 10.8) on 1080p RGB: FP32+FP64-tie path",
+            "value": head["value"], "unit": UNIT, "n_gpus": 1, "steps": K, "warmup": args.warmup,
+            "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": "ACWDDF on the 1920x1080 frames of the DDF workload (sinusoid field + 12 "
+                                   "rectangles, 10% impulses), 24 frames (149 MB) in rotation", "M": M, "N": N,
+                       "lambda": 2, "T": 10.8},
+            "cases": cases, "fp64_path": {"value": head["fp64_value"], "unit": UNIT},
+            "speedup_vs_fp64": head["speedup_vs_fp64"], "gpu_launches": 2 * K, "roofline": roofline,
+            "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
 def run_batch_workload(args):
     """256 uneven images, mixed 3x3/5x5 BVDF/DDF, one persistent launch per
     batch replayed from a CUDA graph, tile shapes from the autotuner."""
@@ -467,7 +534,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=None)
     ap.add_argument("--workload", default="ddf5_1080p",
-                    choices=["ddf5_1080p", "ddf5_4k", "batch", "autograd", "vmf5_1080p"])
+                    choices=["ddf5_1080p", "ddf5_4k", "batch", "autograd", "vmf5_1080p", "acwddf_1080p"])
     ap.add_argument("--shape", type=int, default=None, help="force this FP32 tile shape instead of autotuning")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -481,6 +548,8 @@ def main():
         return run_autograd_workload(args)
     if args.workload == "vmf5_1080p":
         return run_vmf_workload(args)
+    if args.workload == "acwddf_1080p":
+        return run_acwddf_workload(args)
 
     import torch
     import torch.distributed as dist

@@ -124,6 +124,28 @@ int vdf_filter_lp(const uint8_t *img, int M, int N, int win, int filter, double 
                   void *workspace, size_t workspace_bytes, void *stream);
 
 /*
+ * ACWDDF, Eq. (9) (Section 3.2): per pixel, the DDF output (Eq. (3), plain
+ * product, A of dist_mode; Method 2 through Eq. (10)) if
+ *     sum_{k=lambda}^{lambda+2} A(y_k, x_d) * L2(y_k, x_d) > T,
+ * else the centre x_d, where y_k is the centre-weighted VMF output at
+ * smoothing level k: argmin_i sum_j w_j(k) L2(x_i, x_j), w_d(k) = n - 2k + 2,
+ * w_j = 1 otherwise.  Readings: Eq. (9) names the outputs of the test CWDDF^k
+ * but defines CWVMF^k, which are used; the test is strict.  The paper sets
+ * lambda = 2 and T = 10.8.
+ *   lambda     1 .. d - 2 with d = (win*win + 1)/2 (so every level k <= d).
+ *   T          finite threshold.
+ * Other arguments as vdf_filter (filter fixed to the DDF, p = 1/2).  With
+ * VDF_PREC_FP32_RECHECK the DDF choice, each CWVMF level and the switch are
+ * decided in FP32 with certified bounds; a pixel where any of them is open is
+ * recomputed entirely by the FP64 path, so both precisions give the same
+ * result.  Errors: VDF_E_INVALID (also for lambda or T out of range),
+ * VDF_E_WORKSPACE, VDF_E_CUDA.
+ */
+int vdf_filter_acwddf(const uint8_t *img, int M, int N, int win, int dist_mode, int minimax_q, int lambda, double T,
+                      int precision, uint8_t *out, int8_t *index_out, void *workspace, size_t workspace_bytes,
+                      void *stream);
+
+/*
  * The two stages of vdf_filter with VDF_PREC_FP32_RECHECK, for callers that
  * want to time or overlap them separately.  vdf_fp32_pass zeroes the recheck
  * counters, runs the FP32 tile kernel (writing out / index_out for every

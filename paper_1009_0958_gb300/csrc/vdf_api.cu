@@ -4,6 +4,7 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <cmath>
 #include <mutex>
 
 #include "../../include/vdf.h"
@@ -239,6 +240,42 @@ int vdf_filter_lp(const uint8_t *img, int M, int N, int win, int filter, double 
     if (rc != VDF_OK) return rc;
     return fp64_recheck_norm(img, M, N, win, filter, p, dist_mode, minimax_q, out, index_out, workspace,
                              workspace_bytes, stream, norm);
+}
+
+int vdf_filter_acwddf(const uint8_t *img, int M, int N, int win, int dist_mode, int minimax_q, int lambda, double T,
+                      int precision, uint8_t *out, int8_t *index_out, void *workspace, size_t workspace_bytes,
+                      void *stream)
+{
+    int rc = check_filter_args(img, M, N, win, VDF_DDF, 0.5, dist_mode, minimax_q, precision, out, index_out,
+                               nullptr, workspace, workspace_bytes);
+    if (rc != VDF_OK) return rc;
+    const int d1 = (win * win + 1) / 2;   // 1-based centre index: levels lambda .. lambda+2 must stay <= d
+    if (lambda < 1 || lambda > d1 - 2 || !std::isfinite(T)) return VDF_E_INVALID;
+    cudaStream_t st = (cudaStream_t)stream;
+    vdf::TileParams prm = tile_params(img, M, N, 0.5, minimax_q, out, index_out, nullptr,
+                                      precision == VDF_PREC_FP64 ? nullptr : workspace);
+    prm.lam = lambda;
+    prm.T = T;
+    if (precision == VDF_PREC_FP64) return cuda_fail(vdf::run_fp64_acw(prm, win / 2, dist_mode, st));
+    cudaError_t e = cudaMemsetAsync(prm.recheck_ctr, 0, 2 * sizeof(unsigned), st);
+    if (e == cudaSuccess) e = vdf::run_fp32_acw(prm, win / 2, dist_mode, tuned_shape(win, VDF_DDF, dist_mode), st);
+    if (e == cudaSuccess) {
+        vdf::RecheckParams rp{};
+        rp.img = img;
+        rp.out = out;
+        rp.idx = index_out;
+        rp.list = prm.recheck_list;
+        rp.ctr = prm.recheck_ctr;
+        rp.cap = prm.recheck_cap;
+        rp.M = M;
+        rp.N = N;
+        rp.p = 0.5;
+        rp.q = minimax_q;
+        rp.lam = lambda;
+        rp.T = T;
+        e = vdf::run_recheck_acw(rp, win / 2, dist_mode, num_sms() * 16, st);
+    }
+    return cuda_fail(e);
 }
 
 int vdf_filter(const uint8_t *img, int M, int N, int win, int filter, double p, int dist_mode, int minimax_q,

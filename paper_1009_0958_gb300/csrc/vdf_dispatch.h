@@ -33,6 +33,13 @@ cudaError_t run_fp32_lp(const TileParams &prm, int R, int filter, int norm, int 
 cudaError_t run_fp64_lp(const TileParams &prm, int R, int filter, int norm, cudaStream_t st);
 cudaError_t run_recheck_lp(const RecheckParams &prm, int R, int filter, int norm, int blocks, cudaStream_t st);
 
+// ACWDDF (Eq. (9)), uint8 input, every distance mode: the FP32 certified tile
+// kernel (one of kNumShapes32 shapes), the FP64 tile kernel, and the FP64
+// recheck of the pixels the FP32 kernel lists.
+cudaError_t run_fp32_acw(const TileParams &prm, int R, int dist, int shape, cudaStream_t st);
+cudaError_t run_fp64_acw(const TileParams &prm, int R, int dist, cudaStream_t st);
+cudaError_t run_recheck_acw(const RecheckParams &prm, int R, int dist, int blocks, cudaStream_t st);
+
 // FP32 pair terms of n pixel pairs (n x 6 ints), as the FP32 tile kernel computes them.
 cudaError_t run_debug_terms(const int *pairs, int n, int dist, int q, float *angle_out, float *l2_out,
                             cudaStream_t st);

@@ -46,12 +46,18 @@ struct TileParams {
     int M, N, B;
     double p;
     int q;
+    int lam;               // ACWDDF: first smoothing level lambda and threshold T (Eq. (9))
+    double T;
 };
 
-template <int R_, int FILTER_, int DIST_, bool FP64_, bool F32IN_, int TW_, int TH_, int NORM_ = NL2>
+template <int R_, int FILTER_, int DIST_, bool FP64_, bool F32IN_, int TW_, int TH_, int NORM_ = NL2, bool ACW_ = false>
 struct TileCfg {
     static constexpr int R = R_, FILTER = FILTER_, DIST = DIST_, TW = TW_, TH = TH_, NORM = NORM_;
     static constexpr bool FP64 = FP64_, F32IN = F32IN_;
+    // ACWDDF (Eq. (9)): the DDF's aggregates, then the centre-weighted VMF
+    // levels and the switch in the selection
+    static constexpr bool ACW = ACW_;
+    static_assert(!ACW || (FILTER == DDF && NORM == NL2 && !F32IN), "ACWDDF: uint8 DDF at order 2");
     static_assert(FILTER != VMF || DIST == EXACT, "VMF has no angular term");
     static_assert(!F32IN || (FILTER != VMF && NORM == NL2), "float input: BVDF / DDF at order 2");
     // VMF at order 1 or infinity: the aggregates are exact integers in both
@@ -749,13 +755,156 @@ __device__ __forceinline__ int resolve_near(unsigned near, const TileParams &prm
     return argmin();
 }
 
+// ------------------------------------------------ ACWDDF (Eq. (9)) -------
+// After the DDF's choice sel_ddf (Eq. (3), p = 1/2), the centre-weighted VMF
+// at the smoothing levels k = lam .. lam+2: argmin_i sum_j w_j(k) L2(x_i, x_j)
+// with w_d = n - 2k + 2, i.e. S_i + (n - 2k + 1) Lc_i from the member's L2
+// aggregate S_i and its distance Lc_i to the centre; then the switch: the DDF
+// output if sum_k A(y_k, x_d) L2(y_k, x_d) > T, else the centre.
+//
+// FP64 (the FP64 tile kernel and the recheck, bit for bit): S(k) and Lc(k)
+// are the FP64 path's aggregates and terms; every operation is rounded
+// explicitly, so both call sites give the same decision.
+template <int R, int DIST, class SF, class LF, class PF>
+__device__ __forceinline__ int acw_decide64(int sel_ddf, SF S, LF lc, PF px, int lam, double T, int q)
+{
+    constexpr int W = 2 * R + 1, NW = W * W, CENTRE = (NW - 1) / 2;
+    const int4 xd = px(CENTRE);
+    double sum = 0.0;
+#pragma unroll 1
+    for (int lev = 0; lev < 3; ++lev) {
+        const double c = (double)(NW - 2 * (lam + lev) + 1);   // w_d - 1
+        const int y = select64<VMF, NW>([&](int k) { return __dadd_rn(S(k), __dmul_rn(c, lc(k))); });
+        const int4 xy = px(y);
+        double a = aterm64<DIST>(xy, xd, q);
+        if constexpr (DIST == RGB) a = __dadd_rn(__dmul_rn(kSlope64, a), kOffset64);   // Eq. (10)
+        sum = __dadd_rn(sum, __dmul_rn(a, l2term64(xy, xd)));
+    }
+    return sum > T ? sel_ddf : CENTRE;
+}
+
+// FP32: every decision with its certified bound.  Returns the member, or
+// sets *unsure (the caller lists the pixel for the FP64 recheck, which then
+// decides everything) and returns a provisional member.  f: the window's raw
+// slots (sum A, sum L2); P(k): shared-memory index of member k.
+template <class C, class PF>
+__device__ __forceinline__ int acw_select32(const TileParams &prm, const float4 *pix, const Aux *aux,
+                                            const unsigned *keys, const float2 *f, PF P, bool &unsure)
+{
+    constexpr int R = C::R, W = C::W, NW = C::NW, CENTRE = C::CENTRE, DIST = C::DIST;
+    (void)W;
+    // members with provably equal scores: identical vectors (equal keys)
+    auto resolve = [&](unsigned near, auto argmin) -> int {
+        const int first = __ffs(near) - 1;
+        if ((near & (near - 1)) == 0) return first;
+        const unsigned rkey = keys[P(first)];
+        bool same = true;
+#pragma unroll
+        for (int k = 0; k < NW; ++k)
+            if ((near >> k) & 1u) same = same && keys[P(k)] == rkey;
+        if (same) return ((near >> CENTRE) & 1u) ? CENTRE : first;
+        unsure = true;
+        return argmin();
+    };
+    // 1. the DDF, Eq. (3) (p = 1/2: Omega^4 = SA^2 SL^2 with its bound)
+    int sel_ddf;
+    {
+        float2 v[NW];
+        float hi[NW];
+#pragma unroll
+        for (int k = 0; k < NW; ++k) {
+            float sa = f[k].x;
+            if constexpr (DIST == RGB) sa = fmaf(kSlope32, sa, (float)NW * kOffset32);
+            v[k] = score32<R, DDF, DIST>(sa, f[k].y, 0.5f, 2);
+            hi[k] = v[k].x + v[k].y;
+        }
+        const float U = tree_min<NW>(hi);
+        const unsigned near = bit_mask<NW>([&](int k) { return v[k].x - v[k].y <= U; });
+        bool zeros = true;   // all near scores exactly 0 with a zero bound: exact ties
+#pragma unroll
+        for (int k = 0; k < NW; ++k)
+            if ((near >> k) & 1u) zeros = zeros && v[k].x == 0.0f && v[k].y == 0.0f;
+        if (zeros && near) sel_ddf = ((near >> CENTRE) & 1u) ? CENTRE : __ffs(near) - 1;
+        else
+            sel_ddf = resolve(near, [&]() {
+                int arg = 0;
+                float best = v[0].x;
+#pragma unroll
+                for (int k = 1; k < NW; ++k)
+                    if (v[k].x < best) {
+                        best = v[k].x;
+                        arg = k;
+                    }
+                return arg;
+            });
+    }
+    // 2. the centre-weighted VMF levels and the switching sum
+    const float4 xd = pix[P(CENTRE)];
+    float lc[NW];
+#pragma unroll
+    for (int k = 0; k < NW; ++k) {
+        const float4 xk = pix[P(k)];
+        lc[k] = l2term32(xk, xd, fmaf(xk.z, xd.z, fmaf(xk.y, xd.y, xk.x * xd.x)));
+    }
+    constexpr float kS = 6.0f + 4.0f * R;   // relative bound of an L2 aggregate (units of u)
+    float sum = 0.0f, Es = 0.0f;
+#pragma unroll 1
+    for (int lev = 0; lev < 3; ++lev) {
+        const float c = (float)(NW - 2 * (prm.lam + lev) + 1);
+        float sc[NW], hi[NW], lo[NW];
+#pragma unroll
+        for (int k = 0; k < NW; ++k) {
+            sc[k] = fmaf(c, lc[k], f[k].y);
+            const float e = kSafety * kU * (kS * f[k].y + 6.0f * c * lc[k] + sc[k]);
+            hi[k] = sc[k] + e;
+            lo[k] = sc[k] - e;
+        }
+        const float U = tree_min<NW>(hi);
+        const unsigned near = bit_mask<NW>([&](int k) { return lo[k] <= U; });
+        const int y = resolve(near, [&]() {
+            int arg = 0;
+            float best = sc[0];
+#pragma unroll
+            for (int k = 1; k < NW; ++k)
+                if (sc[k] < best) {
+                    best = sc[k];
+                    arg = k;
+                }
+            return arg;
+        });
+        // A(y, x_d) L2(y, x_d): relative (exact, Eq. (10)) or absolute (Method 1) bounds
+        const float4 xy = pix[P(y)];
+        const PairInts r = pair_ints(xy, xd);
+        float a, relA = 0.0f, absA = 0.0f;
+        if constexpr (DIST == EXACT) {
+            a = angle32(r);
+            relA = 16.0f;
+        } else if constexpr (DIST == MINIMAX) {
+            a = minimax32(r, aux[P(y)], aux[P(CENTRE)], prm.q);
+            absA = 24.0f;
+        } else {
+            a = fmaf(kSlope32, chroma32(xy, xd, aux[P(y)], aux[P(CENTRE)]), kOffset32);
+            relA = 13.0f;
+        }
+        const float l = l2term32(xy, xd, r.d);
+        const float t = a * l;
+        sum += t;
+        Es += (fabsf(a) * (relA + 7.0f) + absA) * l + 2.0f * fabsf(t);
+    }
+    const float T = (float)prm.T;
+    Es = kSafety * kU * (Es + fabsf(T)) + 2.0f * (float)fabs((double)T - prm.T);
+    if (fabsf(sum - T) <= Es) unsure = true;
+    return sum > T ? sel_ddf : CENTRE;
+}
+
 // Step 4b of the tile, one thread per output pixel: the member selection
 // from the window's scores (FP32: computed here, in registers, from the raw
 // aggregates) and the stores.
 template <class C>
 __device__ __forceinline__ void select_and_store(const TileParams &prm, int b, int x0, int y0, int tid,
                                                  const typename C::Pix *pix, const unsigned *keys,
-                                                 const typename C::HwT *hw, bool unsafe_tile = false)
+                                                 const typename C::HwT *hw, bool unsafe_tile = false,
+                                                 const Aux *aux = nullptr)
 {
     constexpr int R = C::R, W = C::W, NW = C::NW, PXW = C::PXW;
     using Pix = typename C::Pix;
@@ -765,9 +914,30 @@ __device__ __forceinline__ void select_and_store(const TileParams &prm, int b, i
     const size_t lin = (size_t)gy * prm.N + gx;
     const auto *f = hw + tid * NW;
     int sel;
-    if constexpr (C::FP64) {
+    if constexpr (C::FP64 && C::ACW) {
+        // ACWDDF: the DDF's choice, then the centre-weighted VMF levels and the switch
+        const int sel_ddf = select64<DDF, NW>([&](int k) { return f[k].x; });
+        auto px = [&](int k) { return pix[(ty + k / W) * PXW + (tx + k % W) + 2 * R]; };
+        const Pix xd = px(C::CENTRE);
+        double lc[NW];
+#pragma unroll 1
+        for (int k = 0; k < NW; ++k) lc[k] = l2term64(px(k), xd);
+        sel = acw_decide64<R, C::DIST>(sel_ddf, [&](int k) { return f[k].y; }, [&](int k) { return lc[k]; }, px,
+                                       prm.lam, prm.T, prm.q);
+    } else if constexpr (C::FP64) {
         if constexpr (C::FILTER == DDF) sel = select64<C::FILTER, NW>([&](int k) { return f[k].x; });
         else sel = select64<C::FILTER, NW>([&](int k) { return f[k]; });
+    } else if constexpr (C::ACW) {
+        bool unsure = false;
+        sel = acw_select32<C>(prm, pix, aux, keys, f,
+                              [&](int k) { return (ty + k / W) * PXW + (tx + k % W) + 2 * R; }, unsure);
+        if (unsure) {
+            // the FP64 recheck decides the whole of Eq. (9) (every member)
+            constexpr unsigned ALL = (1u << NW) - 1u;
+            const unsigned slot = atomicAdd(prm.recheck_ctr, 1u);
+            if (slot < prm.recheck_cap) prm.recheck_list[slot] = make_int2(prm.pix_base + gy * prm.N + gx, (int)ALL);
+            else atomicOr(prm.recheck_ctr + 1, 1u);
+        }
     } else {
         int quarter = -1;
         if constexpr (C::FILTER == DDF) {
@@ -1030,7 +1200,7 @@ __device__ __forceinline__ void tile_body(const TileParams &prm, int b, int x0, 
     }
     bool selects = tid < C::TW * C::TH;
     if constexpr (!C::FP64) selects = selects && !prm.dbg_fe;
-    if (selects) select_and_store<C>(prm, b, x0, y0, tid, pix, keys, hw, unsafe);
+    if (selects) select_and_store<C>(prm, b, x0, y0, tid, pix, keys, hw, unsafe, aux);
 }
 
 
@@ -1072,26 +1242,30 @@ struct RecheckParams {
     int M, N;
     double p;
     int q;
+    int lam;           // ACWDDF only
+    double T;
 };
 
 template <int R, int FILTER, int DIST>
 struct RecheckCfg {
+    // (the per-warp region also holds n doubles of L2 aggregates for ACWDDF)
     // one warp per block: consecutive list entries go to different SMs, whose
     // FP64 pipes (1/64 of the FP32 rate) bound the recheck
     static constexpr int W = 2 * R + 1, NW = W * W, WARPS = 1;
     static constexpr int MATS = (FILTER == DDF) ? 2 : 1;
     // per warp: int4 members first (16-byte aligned), then doubles; the size
     // is a multiple of 16 so every warp's region stays 16-byte aligned
-    static constexpr size_t PER_WARP = (sizeof(int4) * NW + sizeof(double) * (MATS * NW * NW + NW) + 15) / 16 * 16;
+    static constexpr size_t PER_WARP = (sizeof(int4) * NW + sizeof(double) * (MATS * NW * NW + 2 * NW) + 15) / 16 * 16;
     static constexpr size_t SMEM = PER_WARP * WARPS;
 };
 
 // Recheck of one listed pixel by one warp.  `base` is the warp's shared
 // memory (RecheckCfg::PER_WARP bytes, 16-byte aligned).
 // F32IN: img and out are float32 B x 3 x M x N and lin = (b M + y) N + x.
-template <int R, int FILTER, int DIST, bool F32IN = false, int NORM = NL2>
+template <int R, int FILTER, int DIST, bool F32IN = false, int NORM = NL2, bool ACW = false>
 __device__ __forceinline__ void recheck_pixel(const void *img, int M, int N, int lin, unsigned mask, void *out,
-                                              int8_t *idx, double p, int q, unsigned char *base, int lane)
+                                              int8_t *idx, double p, int q, unsigned char *base, int lane,
+                                              int lam = 0, double T = 0.0)
 {
     using C = RecheckCfg<R, FILTER, DIST>;
     using PixT = typename std::conditional<F32IN, float4, int4>::type;
@@ -1177,12 +1351,17 @@ __device__ __forceinline__ void recheck_pixel(const void *img, int M, int N, int
             }
             if constexpr (FILTER == DDF && DIST == RGB) sa = __fma_rn(kSlope64, sa, (double)NW * kOffset64);
             f = score64<FILTER>(sa, sl, p);
+            if constexpr (ACW) fs[NW + lane] = sl;   // the member's L2 aggregate
         }
         fs[lane] = f;
     }
     __syncwarp();
     if (lane == 0) {
-        const int sel = select64<FILTER, NW>([&](int k) { return fs[k]; });
+        int sel = select64<FILTER, NW>([&](int k) { return fs[k]; });
+        if constexpr (ACW)   // every member is in the mask: the whole of Eq. (9), as the FP64 tile kernel
+            sel = acw_decide64<R, DIST>(sel, [&](int k) { return fs[NW + k]; },
+                                        [&](int k) { return Ml[k * NW + (NW - 1) / 2]; }, [&](int k) { return px[k]; },
+                                        lam, T, q);
         const PixT v = px[sel];
         if constexpr (F32IN) {
             float *o = (float *)out + (size_t)b * 3 * plane + pl;
@@ -1200,7 +1379,7 @@ __device__ __forceinline__ void recheck_pixel(const void *img, int M, int N, int
     __syncwarp();
 }
 
-template <int R, int FILTER, int DIST, bool F32IN, int NORM>
+template <int R, int FILTER, int DIST, bool F32IN, int NORM, bool ACW>
 __global__ void __launch_bounds__(32) recheck_kernel(const RecheckParams prm)
 {
     using C = RecheckCfg<R, FILTER, DIST>;
@@ -1211,23 +1390,23 @@ __global__ void __launch_bounds__(32) recheck_kernel(const RecheckParams prm)
     const int nwarps = gridDim.x * C::WARPS;
     for (unsigned it = blockIdx.x * C::WARPS + wid; it < count; it += nwarps) {
         const int2 ent = prm.list[it];
-        recheck_pixel<R, FILTER, DIST, F32IN, NORM>(prm.img, prm.M, prm.N, ent.x, (unsigned)ent.y, prm.out, prm.idx,
-                                                    prm.p, prm.q, base, lane);
+        recheck_pixel<R, FILTER, DIST, F32IN, NORM, ACW>(prm.img, prm.M, prm.N, ent.x, (unsigned)ent.y, prm.out,
+                                                         prm.idx, prm.p, prm.q, base, lane, prm.lam, prm.T);
     }
 }
 
-template <int R, int FILTER, int DIST, bool F32IN = false, int NORM = NL2>
+template <int R, int FILTER, int DIST, bool F32IN = false, int NORM = NL2, bool ACW = false>
 cudaError_t launch_recheck(const RecheckParams &prm, int blocks, cudaStream_t st)
 {
     using C = RecheckCfg<R, FILTER, DIST>;
     static bool configured = false;
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(recheck_kernel<R, FILTER, DIST, F32IN, NORM>,
+        cudaError_t e = cudaFuncSetAttribute(recheck_kernel<R, FILTER, DIST, F32IN, NORM, ACW>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    recheck_kernel<R, FILTER, DIST, F32IN, NORM><<<blocks, 32 * C::WARPS, C::SMEM, st>>>(prm);
+    recheck_kernel<R, FILTER, DIST, F32IN, NORM, ACW><<<blocks, 32 * C::WARPS, C::SMEM, st>>>(prm);
     return cudaGetLastError();
 }
 

@@ -44,6 +44,7 @@ def lib():
             L.vdf_host_buffer_bytes.argtypes, L.vdf_host_buffer_bytes.restype = [i, i, i], sz
             L.vdf_filter.argtypes = [P, i, i, i, i, d, i, i, i, P, P, P, P, sz, P]
             L.vdf_filter_lp.argtypes = [P, i, i, i, i, d, i, i, i, i, P, P, P, P, sz, P]
+            L.vdf_filter_acwddf.argtypes = [P, i, i, i, i, i, i, d, i, P, P, P, sz, P]
             L.vdf_filter_host.argtypes = [P, i, i, i, i, d, i, i, i, P, P, P, sz, P]
             L.vdf_filter_f32.argtypes = [P, i, i, i, i, i, d, i, i, i, P, P, P, sz, P]
             L.vdf_backward_f32.argtypes = [P, P, i, i, i, i, P, P]
@@ -56,7 +57,7 @@ def lib():
             L.vdf_debug_sqrt_error.argtypes = [P, P]
             L.vdf_host_frames_buffer_bytes.argtypes, L.vdf_host_frames_buffer_bytes.restype = [i, i, i], sz
             L.vdf_filter_host_frames.argtypes = [P, P, P, i, i, i, i, i, d, i, i, i, P, sz, P]
-            for f in ("vdf_filter", "vdf_filter_lp", "vdf_filter_host", "vdf_workspace_stats", "vdf_debug_fp32_scores",
+            for f in ("vdf_filter", "vdf_filter_lp", "vdf_filter_acwddf", "vdf_filter_host", "vdf_workspace_stats", "vdf_debug_fp32_scores",
                       "vdf_debug_fp32_terms", "vdf_filter_host_frames", "vdf_debug_fp32_terms_f32",
                       "vdf_debug_sqrt_error",
                       "vdf_fp32_pass", "vdf_fp64_recheck", "vdf_filter_f32", "vdf_backward_f32"):
@@ -131,6 +132,29 @@ def filter(img: torch.Tensor, win: int = 3, filter="bvdf", p: float = 0.5, dist=
     _check(lib().vdf_filter_lp(_ptr(img), M, N, win, _code(FILTERS, filter), float(p), ORDERS[order],
                                _code(DISTS, dist), q, prec, _ptr(out), _ptr(index), _ptr(agg), wp, wn,
                                _stream(stream)))
+    return out, index
+
+
+def filter_acwddf(img: torch.Tensor, win: int = 3, dist="exact", q: int = 4, lam: int = 2, T: float = 10.8,
+                  precision="fp32", out: torch.Tensor | None = None, index: torch.Tensor | None = None,
+                  want_index: bool = True, workspace: torch.Tensor | None = None, stream=None):
+    """ACWDDF (Eq. (9)) of an M x N x 3 uint8 CUDA image: the DDF output
+    where the centre-weighted VMF levels lam .. lam+2 differ enough from the
+    centre (switching sum above T), else the centre.  Returns ``(out, index)``."""
+    if not (img.is_cuda and img.dtype == torch.uint8 and img.dim() == 3 and img.shape[2] == 3):
+        raise VdfError("img must be a CUDA uint8 tensor of shape (M, N, 3)")
+    img = img.contiguous()
+    M, N = int(img.shape[0]), int(img.shape[1])
+    if out is None:
+        out = torch.empty_like(img)
+    if index is None and want_index:
+        index = torch.empty((M, N), dtype=torch.int8, device=img.device)
+    prec = _code(PRECISIONS, precision)
+    if workspace is None:
+        workspace = alloc_workspace(M, N, prec, img.device)
+    wp, wn = _aligned(workspace)
+    _check(lib().vdf_filter_acwddf(_ptr(img), M, N, win, _code(DISTS, dist), q, int(lam), float(T), prec, _ptr(out),
+                                   _ptr(index), wp, wn, _stream(stream)))
     return out, index
 
 

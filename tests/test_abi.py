@@ -70,6 +70,18 @@ def test_minkowski_order_checked_on_host(L):
     assert f32 == -6                                     # no VMF on the float path
 
 
+def test_acwddf_arguments_checked_on_host(L):
+    """vdf_filter_acwddf: lambda in [1, d - 2], finite T, the usual checks."""
+    img, out = ctypes.c_void_p(0x10000), ctypes.c_void_p(0x20000)
+
+    def call(win, lam, T, dist=0, q=4, precision=0):
+        return L.vdf_filter_acwddf(img, 8, 8, win, dist, q, lam, T, precision, out, None, None, 0, None)
+    assert call(3, 0, 10.8) == -1 and call(3, 4, 10.8) == -1 and call(5, 12, 10.8) == -1
+    assert call(3, 2, float("inf")) == -1 and call(3, 2, float("nan")) == -1
+    assert call(4, 2, 10.8) == -1 and call(3, 2, 10.8, dist=1, q=5) == -1
+    assert call(3, 2, 10.8, precision=1) == -5    # valid, but no workspace
+
+
 def test_aliasing_and_workspace_checks(L):
     p = ctypes.c_void_p(0x10000)
     assert L.vdf_filter(p, 8, 8, 3, 0, 0.5, 0, 4, 0, p, None, None, None, 0, None) == -1      # out == img
