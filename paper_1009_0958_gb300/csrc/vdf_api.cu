@@ -58,6 +58,10 @@ int num_sms()
     return sms;
 }
 
+// Blocks of the FP64 recheck kernel: consecutive list entries go to
+// different SMs, whose FP64 pipes bound the recheck.
+int recheck_blocks() { return num_sms() * 16; }
+
 // Tile shape of the FP32 kernel per (window, filter, distance mode): shape 0
 // until vdf_autotune or vdf_set_tuned_shape records another.
 std::mutex g_tune_mutex;
@@ -194,7 +198,7 @@ static int fp64_recheck_norm(const uint8_t *img, int M, int N, int win, int filt
     rp.N = N;
     rp.p = p;
     rp.q = minimax_q;
-    return cuda_fail(run_recheck_any(rp, win / 2, filter, dist_mode, norm, num_sms() * 16, (cudaStream_t)stream));
+    return cuda_fail(run_recheck_any(rp, win / 2, filter, dist_mode, norm, recheck_blocks(), (cudaStream_t)stream));
 }
 
 int vdf_fp32_pass(const uint8_t *img, int M, int N, int win, int filter, double p, int dist_mode, int minimax_q,
@@ -273,7 +277,7 @@ int vdf_filter_acwddf(const uint8_t *img, int M, int N, int win, int dist_mode, 
         rp.q = minimax_q;
         rp.lam = lambda;
         rp.T = T;
-        e = vdf::run_recheck_acw(rp, win / 2, dist_mode, num_sms() * 16, st);
+        e = vdf::run_recheck_acw(rp, win / 2, dist_mode, recheck_blocks(), st);
     }
     return cuda_fail(e);
 }
@@ -376,7 +380,7 @@ int vdf_filter_f32(const float *img, int B, int M, int N, int win, int filter, d
         rp.N = N;
         rp.p = p;
         rp.q = minimax_q;
-        e = vdf::run_recheck(rp, win / 2, filter, dist_mode, num_sms() * 16, st, true);
+        e = vdf::run_recheck(rp, win / 2, filter, dist_mode, recheck_blocks(), st, true);
     }
     return cuda_fail(e);
 }

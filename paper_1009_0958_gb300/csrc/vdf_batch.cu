@@ -192,7 +192,6 @@ constexpr auto kGroupConfigure = group_configurers(std::make_integer_sequence<in
 
 // Per-warp shared memory of the largest recheck configuration.
 constexpr size_t kRecheckPerWarp = RecheckCfg<2, DDF, EXACT>::PER_WARP;
-constexpr int kRecheckWarps = 1;   // one warp per block, as the single-image recheck
 
 __global__ void __launch_bounds__(32 * kRecheckWarps) batch_recheck_kernel(const BatchParams bp)
 {

@@ -1246,12 +1246,15 @@ struct RecheckParams {
     double T;
 };
 
+// Warps per recheck block (one listed pixel per warp at a time).
+constexpr int kRecheckWarps = 1;
+
 template <int R, int FILTER, int DIST>
 struct RecheckCfg {
     // (the per-warp region also holds n doubles of L2 aggregates for ACWDDF)
     // one warp per block: consecutive list entries go to different SMs, whose
     // FP64 pipes (1/64 of the FP32 rate) bound the recheck
-    static constexpr int W = 2 * R + 1, NW = W * W, WARPS = 1;
+    static constexpr int W = 2 * R + 1, NW = W * W, WARPS = kRecheckWarps;
     static constexpr int MATS = (FILTER == DDF) ? 2 : 1;
     // per warp: int4 members first (16-byte aligned), then doubles; the size
     // is a multiple of 16 so every warp's region stays 16-byte aligned
@@ -1380,7 +1383,7 @@ __device__ __forceinline__ void recheck_pixel(const void *img, int M, int N, int
 }
 
 template <int R, int FILTER, int DIST, bool F32IN, int NORM, bool ACW>
-__global__ void __launch_bounds__(32) recheck_kernel(const RecheckParams prm)
+__global__ void __launch_bounds__(32 * kRecheckWarps) recheck_kernel(const RecheckParams prm)
 {
     using C = RecheckCfg<R, FILTER, DIST>;
     extern __shared__ __align__(16) unsigned char smem[];
