@@ -120,3 +120,37 @@ def test_plan_rejects_bad_descriptors(V):
         V.Plan([dict(img=x, win=3)], dist="minimax")
     with pytest.raises(V.VdfError):
         V.Plan([dict(img=x, win=3, filter="ddf", p=2.0)])
+
+
+@pytest.mark.parametrize("persistent", [False, True])
+def test_full_size_batch_workload(V, persistent):
+    """The benchmark's batch (256 images, sides log-uniform in [64, 2048],
+    150.8 Mpix, mixed 3x3/5x5 BVDF/DDF, tuned shapes) in the launch
+    configuration the bench times (graph replay): every image equals the
+    single-image FP32 path, and the oracle on 400 sampled pixels."""
+    import oracle
+    import bench
+    oracle.build()
+    imgs = bench.batch_images(256, 4242)
+    rng = np.random.default_rng(7)
+    cfgs = [(int(rng.choice([3, 5])), str(rng.choice(["bvdf", "ddf"]))) for _ in imgs]
+    probe = torch.from_numpy(bench.frames(1)[0]).cuda()
+    for win in (3, 5):
+        for f in ("bvdf", "ddf"):
+            V.autotune(probe, win, f, 0.25, reps=2)
+    items = [dict(img=torch.from_numpy(x).cuda(), win=w, filter=f, p=0.25) for x, (w, f) in zip(imgs, cfgs)]
+    plan = V.Plan(items, persistent=persistent)
+    plan.graph_launch()
+    plan.graph_launch()
+    torch.cuda.synchronize()
+    rechecked, overflow = plan.stats()
+    assert overflow == 0 and rechecked > 0
+    check_against_single(V, plan, "fp32")
+    srng = np.random.default_rng(8)
+    for k in srng.choice(len(imgs), 40, replace=False):
+        it, img = plan.items[k], imgs[k]
+        M, N = img.shape[:2]
+        pix = srng.integers(0, M * N, 10)
+        ref = oracle.filter_u8(img, it["win"], it["filter"], 0.25, "exact", 4, pixels=pix)
+        assert np.array_equal(it["index"].cpu().numpy().reshape(-1)[pix], ref["idx"])
+        assert np.array_equal(it["out"].cpu().numpy().reshape(-1, 3)[pix], ref["out"])
