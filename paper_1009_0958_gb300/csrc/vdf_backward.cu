@@ -123,16 +123,21 @@ __global__ void __launch_bounds__(256) backward_gather(const float *__restrict__
             return si[ty + r][c];
         }
     };
+    // Per output pixel: the sources as a bit mask over the neighbourhood
+    // (bit (dy+R) W + (dx+R)), from the index bytes alone; then only the
+    // sources' gradients are read, lowest bit first, i.e. in the raster order
+    // of p.  On average one of the (2R+1)^2 neighbours is a source, so this
+    // reads a fraction of what testing each neighbour's gradient would.
     float acc[3][kQ];
     auto gather = [&](auto fast) {
 #pragma unroll
         for (int j = 0; j < kQ; ++j) {
-            acc[0][j] = acc[1][j] = acc[2][j] = 0.0f;
+            unsigned mask = 0;
 #pragma unroll
             for (int dy = -R; dy <= R; ++dy)
 #pragma unroll
                 for (int dx = -R; dx <= R; ++dx) {
-                    const int r = ty + R + dy, c = x0 + j + C0 + dx;
+                    const int c = x0 + j + C0 + dx;
                     const int i = member(R + dy, c);
                     bool hit;
                     if constexpr (decltype(fast)::value) {
@@ -142,12 +147,20 @@ __global__ void __launch_bounds__(256) backward_gather(const float *__restrict__
                         const int sx = min(max(X0 + j + dx + i % W - R, 0), N - 1);
                         hit = i >= 0 && sy == y && sx == X0 + j;
                     }
-                    if (hit) {
-                        acc[0][j] += sg[0][r][c];
-                        acc[1][j] += sg[1][r][c];
-                        acc[2][j] += sg[2][r][c];
-                    }
+                    mask |= (hit ? 1u : 0u) << ((dy + R) * W + (dx + R));
                 }
+            float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f;
+            while (mask) {
+                const int n = __ffs(mask) - 1;
+                mask &= mask - 1;
+                const int r = ty + n / W, c = x0 + j + C0 + n % W - R;
+                a0 += sg[0][r][c];
+                a1 += sg[1][r][c];
+                a2 += sg[2][r][c];
+            }
+            acc[0][j] = a0;
+            acc[1][j] = a1;
+            acc[2][j] = a2;
         }
     };
     // the branch is taken once per thread, outside the unrolled loops
