@@ -86,6 +86,17 @@ SMS, FP32_LANES_PER_SM = 152, 128
 TRAFFIC_BY_SOURCE = {"b20176bf23c200f8": 6296064}   # profiles/tile_kernel_fp32_ddf5_1080p.md
 
 
+# DRAM bytes per launch of the backward gather on the differentiable workload
+# (profiles/backward_gather_autograd_32x512x512.md), keyed like the above by a
+# hash of vdf_backward.cu.
+BACKWARD_TRAFFIC_BY_SOURCE = {"cad5526a8ad6cc4c": 167979008}
+
+
+def backward_source_hash() -> str:
+    with open(os.path.join(ROOT, "paper_1009_0958_gb300", "csrc", "vdf_backward.cu"), "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()[:16]
+
+
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
     for f in ("vdf_tile.cuh", "vdf_internal.cuh", "vdf_fp32.cu"):
@@ -519,7 +530,8 @@ def run_autograd_workload(args):
             "forward_ms": fwd, "backward_ms": bwd, "forward_fp64_ms": fwd64,
             "forward_recheck_fraction": rechecked / px,
             "roofline": {"bound": "hbm", "kernel": "vdf::backward_gather<R=1>", "achieved": bw,
-                         "peak": 6793.1, "unit": "GB/s", "frac": bw / 6793.1, "traffic": None,
+                         "peak": 6793.1, "unit": "GB/s", "frac": bw / 6793.1,
+                         "traffic": BACKWARD_TRAFFIC_BY_SOURCE.get(backward_source_hash()),
                          "algorithmic_bytes_per_pixel": 25},
             "gpu_launches": 2 * K, "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
