@@ -12,8 +12,6 @@
 // (including at the borders, where clamping only moves sources inward), so
 // each thread gathers over the (2R+1)^2 neighbourhood of its own q in a fixed
 // order: no atomics, bit-reproducible.
-#include <type_traits>
-
 #include "vdf_dispatch.h"
 
 namespace vdf {
@@ -22,11 +20,11 @@ namespace {
 
 // A block gathers a kTX x kTY tile: the gradients and indices of the tile
 // and a ring around it are first staged in shared memory (entries outside
-// the image get index -1), then each thread gathers for kQ pixels of one row
-// from there.  For each q the sources are added in raster order of p.  A
-// thread whose sources all lie at least R pixels inside the image tests a
-// source with one compare (p selects q exactly when its member offset is
-// q - p); threads near the border apply the clamped test.
+// the image get index -1).  Then every staged pixel p within R of the tile
+// computes its source q = src(p) and, when q lies in the tile, sets bit
+// (p - q + (R, R)) in q's source mask (a shared-memory OR).  Finally each
+// thread gathers for kQ pixels of one row: it adds the gradients of the set
+// bits, lowest first, i.e. in raster order of p.
 //
 // Staging: with VEC (N a multiple of 4, 16-byte aligned gradients) rows are
 // read as float4 / 32-bit words over columns bx - 4 .. bx + kTX + 3 (every
@@ -43,11 +41,13 @@ __global__ void __launch_bounds__(256) backward_gather(const float *__restrict__
     constexpr int HX = kTX + 2 * C0;
     __shared__ __align__(16) float sg[3][HY][HX];
     __shared__ __align__(16) int8_t si[HY][HX];
+    __shared__ unsigned qm[kTY][kTX];   // per pixel of the tile: its sources, bit (dy+R) W + (dx+R)
     const int bx = blockIdx.x * kTX, by = blockIdx.y * kTY, b = blockIdx.z;
     const size_t plane = (size_t)M * N;
     const int8_t *ib = idx + (size_t)b * plane;
     const float *g = gy + (size_t)b * 3 * plane;
     const int tid = threadIdx.x;
+    for (int e = tid; e < kTY * kTX; e += 256) (&qm[0][0])[e] = 0u;
     if constexpr (VEC) {
         // HY rows x HX / 4 vectors; each thread issues all its loads first
         constexpr int NV = HY * (HX / 4), PER = (NV + 255) / 256;
@@ -102,72 +102,39 @@ __global__ void __launch_bounds__(256) backward_gather(const float *__restrict__
         }
     }
     __syncthreads();
+    // every pixel p within R of the tile marks itself in its source's mask
+    constexpr int SW = kTX + 2 * R, NS = HY * SW;
+    for (int e = tid; e < NS; e += 256) {
+        const int r = e / SW, cc = e - r * SW;            // p at tile row r - R, column cc - R
+        const int i = si[r][cc + C0 - R];
+        if (i < 0) continue;                              // outside the image
+        const int py = by + r - R, px = bx + cc - R;
+        const int qy = min(max(py + i / W - R, 0), M - 1), qx = min(max(px + i % W - R, 0), N - 1);
+        const int ty = qy - by, tx = qx - bx;
+        if (ty >= 0 && ty < kTY && tx >= 0 && tx < kTX)
+            atomicOr(&qm[ty][tx], 1u << ((py - qy + R) * W + (px - qx + R)));
+    }
+    __syncthreads();
     const int ty = tid / (kTX / kQ), x0 = (tid % (kTX / kQ)) * kQ;   // tile coordinates
     const int y = by + ty, X0 = bx + x0;
     if (y >= M || X0 >= N) return;
-    // the index bytes of the thread's neighbourhood: VEC reads the three
-    // words at staged columns x0, x0 + 4, x0 + 8 of each row (columns
-    // x0 + 4 - R .. x0 + 7 + R are needed), otherwise byte by byte
-    unsigned iw[W][3];
-    if constexpr (VEC) {
-#pragma unroll
-        for (int r = 0; r < W; ++r)
-#pragma unroll
-            for (int k = 0; k < 3; ++k) iw[r][k] = *reinterpret_cast<const unsigned *>(&si[ty + r][x0 + 4 * k]);
-    }
-    auto member = [&](int r, int c) -> int {   // r = row in the neighbourhood, c = staged column
-        if constexpr (VEC) {
-            const int k = c - x0;                  // 0 .. 11, known at compile time after unrolling
-            return (int)(int8_t)(iw[r][k >> 2] >> (8 * (k & 3)));
-        } else {
-            return si[ty + r][c];
-        }
-    };
-    // Per output pixel: the sources as a bit mask over the neighbourhood
-    // (bit (dy+R) W + (dx+R)), from the index bytes alone; then only the
-    // sources' gradients are read, lowest bit first, i.e. in the raster order
-    // of p.  On average one of the (2R+1)^2 neighbours is a source, so this
-    // reads a fraction of what testing each neighbour's gradient would.
     float acc[3][kQ];
-    auto gather = [&](auto fast) {
 #pragma unroll
-        for (int j = 0; j < kQ; ++j) {
-            unsigned mask = 0;
-#pragma unroll
-            for (int dy = -R; dy <= R; ++dy)
-#pragma unroll
-                for (int dx = -R; dx <= R; ++dx) {
-                    const int c = x0 + j + C0 + dx;
-                    const int i = member(R + dy, c);
-                    bool hit;
-                    if constexpr (decltype(fast)::value) {
-                        hit = i == (R - dy) * W + (R - dx);
-                    } else {
-                        const int sy = min(max(y + dy + i / W - R, 0), M - 1);
-                        const int sx = min(max(X0 + j + dx + i % W - R, 0), N - 1);
-                        hit = i >= 0 && sy == y && sx == X0 + j;
-                    }
-                    mask |= (hit ? 1u : 0u) << ((dy + R) * W + (dx + R));
-                }
-            float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f;
-            while (mask) {
-                const int n = __ffs(mask) - 1;
-                mask &= mask - 1;
-                const int r = ty + n / W, c = x0 + j + C0 + n % W - R;
-                a0 += sg[0][r][c];
-                a1 += sg[1][r][c];
-                a2 += sg[2][r][c];
-            }
-            acc[0][j] = a0;
-            acc[1][j] = a1;
-            acc[2][j] = a2;
+    for (int j = 0; j < kQ; ++j) {
+        unsigned mask = qm[ty][x0 + j];
+        float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f;
+        while (mask) {
+            const int n = __ffs(mask) - 1;
+            mask &= mask - 1;
+            const int r = ty + n / W, c = x0 + j + C0 + n % W - R;
+            a0 += sg[0][r][c];
+            a1 += sg[1][r][c];
+            a2 += sg[2][r][c];
         }
-    };
-    // the branch is taken once per thread, outside the unrolled loops
-    if (y >= 2 * R && y < M - 2 * R && X0 >= 2 * R && X0 + kQ - 1 + 2 * R < N)
-        gather(std::true_type{});
-    else
-        gather(std::false_type{});
+        acc[0][j] = a0;
+        acc[1][j] = a1;
+        acc[2][j] = a2;
+    }
     float *o = gx + (size_t)b * 3 * plane + (size_t)y * N + X0;
     if (VEC && X0 + kQ <= N) {
 #pragma unroll
