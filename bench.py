@@ -89,7 +89,7 @@ TRAFFIC_BY_SOURCE = {"b4fb3d4584f2b58c": 6296064}   # profiles/tile_kernel_fp32_
 # DRAM bytes per launch of the backward gather on the differentiable workload
 # (profiles/backward_gather_autograd_32x512x512.md), keyed like the above by a
 # hash of vdf_backward.cu.
-BACKWARD_TRAFFIC_BY_SOURCE = {"b4fb3d4584f2b58c": 6296064}
+BACKWARD_TRAFFIC_BY_SOURCE = {"53fb82fb4df342a0": 166982400}
 
 
 def backward_source_hash() -> str:
