@@ -23,6 +23,7 @@
 
 #include <algorithm>
 #include <array>
+#include <atomic>
 #include <mutex>
 #include <vector>
 
@@ -244,7 +245,7 @@ struct vdf_plan {
     long long total_pixels = 0;
     int q = 4;
     int sms = 1;
-    bool persistent = false;   // tile kernels in the persistent work-queue form
+    std::atomic<bool> persistent{false};   // tile kernels in the persistent work-queue form
     std::mutex mutex;
     cudaGraphExec_t exec = nullptr;
     void *exec_ws = nullptr;
@@ -406,7 +407,7 @@ int vdf_filter_batch(vdf_plan *plan, void *workspace, size_t workspace_bytes, vo
     const int ngroups = (int)plan->groups.size();
     cudaError_t e = cudaMemsetAsync(workspace, 0, (2 + ngroups) * sizeof(unsigned), st);
     for (int g = 0; g < ngroups && e == cudaSuccess; ++g)
-        e = vdf::kGroupLaunch[plan->groups[g].cfg](plan_params(plan, workspace, g), sms, st, plan->persistent);
+        e = vdf::kGroupLaunch[plan->groups[g].cfg](plan_params(plan, workspace, g), sms, st, plan->persistent.load());
     if (e == cudaSuccess) {
         vdf::batch_recheck_kernel<<<sms * 16, 32 * vdf::kRecheckWarps, vdf::kRecheckPerWarp * vdf::kRecheckWarps, st>>>(
             plan_params(plan, workspace, -1));
@@ -455,7 +456,7 @@ int vdf_plan_set_persistent(vdf_plan *plan, int persistent)
 {
     if (!plan) return VDF_E_INVALID;
     std::lock_guard<std::mutex> lock(plan->mutex);
-    if (plan->persistent != (persistent != 0) && plan->exec) {
+    if (plan->persistent.load() != (persistent != 0) && plan->exec) {
         cudaGraphExecDestroy(plan->exec);   // the captured graph holds the other form
         plan->exec = nullptr;
         plan->exec_ws = nullptr;
