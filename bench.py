@@ -83,13 +83,13 @@ SMS, FP32_LANES_PER_SM = 152, 128
 
 # DRAM bytes per launch of the FP32 tile kernel, from one ncu capture, keyed
 # by a hash of the kernel sources it was taken on (null once they change).
-TRAFFIC_BY_SOURCE = {"b4fb3d4584f2b58c": 6296064}   # profiles/tile_kernel_fp32_ddf5_1080p.md
+TRAFFIC_BY_SOURCE = {"68d1641ecb2a01ef": 6296320}   # profiles/tile_kernel_fp32_ddf5_1080p.md
 
 
 # DRAM bytes per launch of the backward gather on the differentiable workload
 # (profiles/backward_gather_autograd_32x512x512.md), keyed like the above by a
 # hash of vdf_backward.cu.
-BACKWARD_TRAFFIC_BY_SOURCE = {"53fb82fb4df342a0": 166982400}
+BACKWARD_TRAFFIC_BY_SOURCE = {"68d1641ecb2a01ef": 6296320}
 
 
 def backward_source_hash() -> str:

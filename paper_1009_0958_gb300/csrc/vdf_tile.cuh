@@ -26,6 +26,7 @@
 // aggregate adds the row sums in the order dy = 0, +1, -1, +2, -2, ...
 #pragma once
 
+#include <atomic>
 #include <type_traits>
 #include <utility>
 
@@ -1214,11 +1215,12 @@ __global__ void __launch_bounds__(C::NT, C::MINB) tile_kernel(const TileParams p
 template <class C>
 cudaError_t launch_tile(const TileParams &prm, cudaStream_t st)
 {
-    static bool configured = false;
-    if (!configured) {
+    // set once per instantiation; concurrent first calls may both set it (idempotent)
+    static std::atomic<bool> configured{false};
+    if (!configured.load(std::memory_order_acquire)) {
         cudaError_t e = cudaFuncSetAttribute(tile_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
         if (e != cudaSuccess) return e;
-        configured = true;
+        configured.store(true, std::memory_order_release);
     }
     dim3 grid((prm.N + C::TW - 1) / C::TW, (prm.M + C::TH - 1) / C::TH, prm.B);
     tile_kernel<C><<<grid, C::NT, C::SMEM, st>>>(prm);
@@ -1402,12 +1404,12 @@ template <int R, int FILTER, int DIST, bool F32IN = false, int NORM = NL2, bool 
 cudaError_t launch_recheck(const RecheckParams &prm, int blocks, cudaStream_t st)
 {
     using C = RecheckCfg<R, FILTER, DIST>;
-    static bool configured = false;
-    if (!configured) {
+    static std::atomic<bool> configured{false};
+    if (!configured.load(std::memory_order_acquire)) {
         cudaError_t e = cudaFuncSetAttribute(recheck_kernel<R, FILTER, DIST, F32IN, NORM, ACW>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
         if (e != cudaSuccess) return e;
-        configured = true;
+        configured.store(true, std::memory_order_release);
     }
     recheck_kernel<R, FILTER, DIST, F32IN, NORM, ACW><<<blocks, 32 * C::WARPS, C::SMEM, st>>>(prm);
     return cudaGetLastError();
