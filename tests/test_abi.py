@@ -115,3 +115,48 @@ def test_float_debug_entries_checked_on_host(L):
     assert L.vdf_debug_fp32_terms_f32(None, 4, None, None, None) == -1
     assert L.vdf_debug_fp32_terms_f32(ctypes.c_void_p(0x10000), -1, None, None, None) == -1
     assert L.vdf_debug_sqrt_error(None, None) == -1
+
+
+def test_plan_host_logic(L):
+    """vdf_plan_create validates descriptors and sizes the workspace on the
+    host: counters (256 B), descriptors (56 B each, 16-byte rounded), one int
+    per work item (tiles of the tuned shape, 32x16 by default) and one
+    recheck entry (8 B) per pixel.  No device memory is touched."""
+    from paper_1009_0958_gb300 import vdf
+    P = ctypes.c_void_p
+    L.vdf_plan_create.argtypes = [ctypes.POINTER(P), P, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    L.vdf_plan_create.restype = ctypes.c_int
+    L.vdf_plan_workspace_bytes.argtypes, L.vdf_plan_workspace_bytes.restype = [P], ctypes.c_size_t
+    L.vdf_plan_set_persistent.argtypes, L.vdf_plan_set_persistent.restype = [P, ctypes.c_int], ctypes.c_int
+    L.vdf_plan_destroy.argtypes, L.vdf_plan_destroy.restype = [P], None
+    for win in (3, 5):
+        for f in (0, 1):
+            assert L.vdf_set_tuned_shape(win, f, 0, 0) == 0
+    dims = [(40, 70, 3, 0), (1, 1, 5, 1), (100, 33, 5, 0), (17, 200, 3, 1), (64, 64, 5, 1)]
+
+    def descs(items, base=0x100000):
+        arr = (vdf.ImageDesc * len(items))()
+        for k, (M, N, win, f) in enumerate(items):
+            a = base + k * (1 << 24)
+            arr[k] = vdf.ImageDesc(a, a + (1 << 23), 0, M, N, win, f, 0.25)
+        return arr
+
+    h = P()
+    arr = descs(dims)
+    assert L.vdf_plan_create(ctypes.byref(h), ctypes.cast(arr, P), len(dims), 0, 4) == 0
+    tiles = sum(-(-M // 16) * -(-N // 32) for M, N, _, _ in dims)
+    pixels = sum(M * N for M, N, _, _ in dims)
+    up16 = lambda v: (v + 15) // 16 * 16
+    assert L.vdf_plan_workspace_bytes(h) == 256 + up16(56 * len(dims)) + up16(4 * tiles) + 8 * pixels
+    assert L.vdf_plan_set_persistent(h, 1) == 0 and L.vdf_plan_set_persistent(h, 0) == 0
+    L.vdf_plan_destroy(h)
+    bad = [[(0, 5, 3, 0)], [(5, 5, 4, 0)], [(5, 5, 3, 2)], [(5, 5, 3, 7)]]
+    for items in bad:
+        h = P()
+        assert L.vdf_plan_create(ctypes.byref(h), ctypes.cast(descs(items), P), 1, 0, 4) == -1
+    h = P()
+    assert L.vdf_plan_create(ctypes.byref(h), ctypes.cast(descs(dims[:1]), P), 1, 1, 4) == -6   # exact mode only
+    assert L.vdf_plan_create(ctypes.byref(h), None, 1, 0, 4) == -1
+    over = (vdf.ImageDesc * 1)()
+    over[0] = vdf.ImageDesc(0x100000, 0x100010, 0, 8, 8, 3, 0, 0.5)   # out overlaps img
+    assert L.vdf_plan_create(ctypes.byref(h), ctypes.cast(over, P), 1, 0, 4) == -1
