@@ -68,8 +68,10 @@ typedef enum {
     VDF_OK = 0,
     VDF_E_INVALID = -1,     /* null pointer, bad size, bad win / p / q, aliasing */
     VDF_E_CUDA = -2,        /* a CUDA launch or copy failed (see vdf_last_cuda_error) */
-    VDF_E_OVERFLOW = -3,    /* recheck list larger than the workspace allows */
-    VDF_E_TIMEOUT = -4,     /* a bounded device-side wait gave up */
+    VDF_E_OVERFLOW = -3,    /* reserved, never returned: the recheck list has an
+                               entry for every pixel, so it cannot overflow */
+    VDF_E_TIMEOUT = -4,     /* reserved, never returned: no kernel of this
+                               library waits on the device */
     VDF_E_WORKSPACE = -5,   /* workspace missing or smaller than required */
     VDF_E_UNSUPPORTED = -6  /* valid request this build does not implement */
 } vdf_status;
@@ -166,6 +168,29 @@ int vdf_fp64_recheck(const uint8_t *img, int M, int N, int win, int filter, doub
 int vdf_workspace_stats(const void *workspace, int64_t *rechecked, int32_t *overflow, void *stream);
 
 /*
+ * Counters of the last FP32 call (vdf_filter / vdf_fp32_pass / vdf_filter_lp /
+ * vdf_filter_acwddf / vdf_filter_f32 with VDF_PREC_FP32_RECHECK, or
+ * vdf_filter_batch) that used `workspace`:
+ *   rechecked        pixels listed for the FP64 recheck (their near-minimal
+ *                    members were not separated by the certified bounds);
+ *   structural_ties  pixels with several near-minimal members that the FP32
+ *                    path proved equal (identical vectors; collinear ones for
+ *                    BVDF; exact zeros; equal integer scores of the VMF at
+ *                    orders 1 and infinity), decided by the tie rule without
+ *                    a recheck (Section II defines the selection as an
+ *                    argmin; the tie rule is this library's);
+ *   overflow         always 0 (the list has an entry per pixel).
+ * Synchronises `stream` and copies 256 bytes to the host.  Errors:
+ * VDF_E_INVALID for a null pointer, VDF_E_CUDA.
+ */
+typedef struct {
+    int64_t rechecked;
+    int64_t structural_ties;
+    int32_t overflow;
+} vdf_stats;
+int vdf_read_stats(const void *workspace, vdf_stats *stats, void *stream);
+
+/*
  * Same as vdf_filter with host buffers: copies img (M*N*3 bytes, host) to
  * the device, filters, copies out (M*N*3) and index_out (M*N, may be NULL)
  * back, and waits for the stream.  dev_buffer is device scratch of
@@ -232,6 +257,8 @@ int vdf_filter_f32(const float *img, int B, int M, int N, int win, int filter, d
  * neighbourhood in a fixed order (deterministic, no atomics).
  *   grad_y, grad_x: device, B x 3 x M x N float32 (must not overlap);
  *   index: device, B x M x N int8 from vdf_filter_f32 with the same win.
+ *          A byte outside 0 .. win*win - 1 (e.g. from a map made with a
+ *          different window) selects no source: its pixel passes no gradient.
  * There is no counterpart in the paper (it does not differentiate the
  * filters); this is the exact gradient of the selection away from ties.
  */
@@ -251,6 +278,10 @@ int vdf_backward_f32(const float *grad_y, const int8_t *index, int B, int M, int
  *     larger images return VDF_E_WORKSPACE and launch nothing.
  *   - The first call on a device looks up the array's device address (which
  *     may load the library's device code): make it before any stream capture.
+ *     The address is kept for the process; after cudaDeviceReset on a
+ *     device, do not call this function on that device again.
+ *   - Arguments are checked as by vdf_filter (VDF_E_INVALID) before the size
+ *     limit (VDF_E_WORKSPACE).
  *   - All calls share the array: calls that overlap on the GPU race and must
  *     be serialised by the caller.
  * Other arguments, results and errors as vdf_filter.

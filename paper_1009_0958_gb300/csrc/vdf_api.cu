@@ -25,7 +25,7 @@ int cuda_fail(cudaError_t e)
 // Workspace of the FP32 path: two counters, padding to 256 bytes, then one
 // {pixel id, member mask} int2 entry per pixel (the recheck list can never
 // overflow).
-constexpr size_t kCtrBytes = 256;
+constexpr size_t kCtrBytes = vdf::kCounterBlockBytes;
 
 bool valid_common(int M, int N, int win, int filter, double p, int dist, int q, int prec)
 {
@@ -45,17 +45,18 @@ bool overlaps(const void *a, size_t na, const void *b, size_t nb)
     return x < y + nb && y < x + na;
 }
 
+// SM count of the current device (looked up once per device)
 int num_sms()
 {
-    static int sms = 0;
-    static std::once_flag once;
-    std::call_once(once, [] {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (sms <= 0) sms = 1;
-    });
-    return sms;
+    static std::atomic<int> sms[vdf::kMaxDevices];
+    const int dev = vdf::current_device();
+    if (dev < 0) return 1;
+    int n = sms[dev].load(std::memory_order_relaxed);
+    if (n <= 0) {
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) return 1;
+        sms[dev].store(n, std::memory_order_relaxed);
+    }
+    return n;
 }
 
 // Blocks of the FP64 recheck kernel: consecutive list entries go to
@@ -136,6 +137,21 @@ static int check_filter_args(const uint8_t *img, int M, int N, int win, int filt
     return VDF_OK;
 }
 
+}  // extern "C"
+
+// Argument checks of the FP32 path without its workspace (vdf_filter_noalloc
+// supplies its own scratch); dispatch-internal, declared in vdf_dispatch.h.
+int vdf::check_args_no_workspace(const uint8_t *img, int M, int N, int win, int filter, double p, int dist_mode,
+                                 int minimax_q, const uint8_t *out, const int8_t *index_out)
+{
+    if (filter == VDF_VMF) dist_mode = VDF_DIST_EXACT;
+    if (!valid_common(M, N, win, filter, p, dist_mode, minimax_q, VDF_PREC_FP32_RECHECK)) return VDF_E_INVALID;
+    return check_filter_args(img, M, N, win, filter, p, dist_mode, minimax_q, VDF_PREC_FP64, out, index_out, nullptr,
+                             nullptr, 0);
+}
+
+extern "C" {
+
 static vdf::TileParams tile_params(const uint8_t *img, int M, int N, double p, int q, uint8_t *out, int8_t *idx,
                                    double *agg, void *workspace)
 {
@@ -166,7 +182,7 @@ static int fp32_pass_shape(const uint8_t *img, int M, int N, int win, int filter
     if (rc != VDF_OK) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     const vdf::TileParams prm = tile_params(img, M, N, p, minimax_q, out, index_out, nullptr, workspace);
-    cudaError_t e = cudaMemsetAsync(prm.recheck_ctr, 0, 2 * sizeof(unsigned), st);
+    cudaError_t e = cudaMemsetAsync(prm.recheck_ctr, 0, vdf::kCounterBlockBytes, st);
     if (e == cudaSuccess) e = run_tile32(prm, win / 2, filter, dist_mode, norm, shape, st);
     return cuda_fail(e);
 }
@@ -261,7 +277,7 @@ int vdf_filter_acwddf(const uint8_t *img, int M, int N, int win, int dist_mode, 
     prm.lam = lambda;
     prm.T = T;
     if (precision == VDF_PREC_FP64) return cuda_fail(vdf::run_fp64_acw(prm, win / 2, dist_mode, st));
-    cudaError_t e = cudaMemsetAsync(prm.recheck_ctr, 0, 2 * sizeof(unsigned), st);
+    cudaError_t e = cudaMemsetAsync(prm.recheck_ctr, 0, vdf::kCounterBlockBytes, st);
     if (e == cudaSuccess) e = vdf::run_fp32_acw(prm, win / 2, dist_mode, tuned_shape(win, VDF_DDF, dist_mode), st);
     if (e == cudaSuccess) {
         vdf::RecheckParams rp{};
@@ -300,6 +316,20 @@ int vdf_workspace_stats(const void *workspace, int64_t *rechecked, int32_t *over
     if (e != cudaSuccess) return cuda_fail(e);
     if (rechecked) *rechecked = h[0];
     if (overflow) *overflow = (int32_t)h[1];
+    return VDF_OK;
+}
+
+int vdf_read_stats(const void *workspace, vdf_stats *stats, void *stream)
+{
+    if (!workspace || !stats) return VDF_E_INVALID;
+    unsigned h[vdf::kCounterBlockBytes / sizeof(unsigned)] = {};
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(h, workspace, sizeof(h), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e);
+    stats->rechecked = h[0];
+    stats->overflow = (int32_t)h[1];
+    stats->structural_ties = h[vdf::kTieCounter];
     return VDF_OK;
 }
 
@@ -366,7 +396,7 @@ int vdf_filter_f32(const float *img, int B, int M, int N, int win, int filter, d
     prm.recheck_ctr = (unsigned *)workspace;
     prm.recheck_list = (int2 *)((char *)workspace + kCtrBytes);
     prm.recheck_cap = (unsigned)((size_t)B * M * N);
-    cudaError_t e = cudaMemsetAsync(prm.recheck_ctr, 0, 2 * sizeof(unsigned), st);
+    cudaError_t e = cudaMemsetAsync(prm.recheck_ctr, 0, vdf::kCounterBlockBytes, st);
     if (e == cudaSuccess) e = vdf::run_fp32_f32in(prm, win / 2, filter, st);
     if (e == cudaSuccess) {
         vdf::RecheckParams rp{};

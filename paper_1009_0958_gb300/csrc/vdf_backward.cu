@@ -107,7 +107,9 @@ __global__ void __launch_bounds__(256) backward_gather(const float *__restrict__
     for (int e = tid; e < NS; e += 256) {
         const int r = e / SW, cc = e - r * SW;            // p at tile row r - R, column cc - R
         const int i = si[r][cc + C0 - R];
-        if (i < 0) continue;                              // outside the image
+        // outside the image (-1), or not a member index of this window size
+        // (an index map made with another window): selects nothing
+        if ((unsigned)i >= (unsigned)(W * W)) continue;
         const int py = by + r - R, px = bx + cc - R;
         const int qy = min(max(py + i / W - R, 0), M - 1), qx = min(max(px + i % W - R, 0), N - 1);
         const int ty = qy - by, tx = qx - bx;

@@ -224,7 +224,8 @@ __global__ void __launch_bounds__(32 * kRecheckWarps) batch_recheck_kernel(const
 
 // recheck count, overflow flag, one work counter per configuration
 constexpr size_t kCtrBytes = 256;
-static_assert((2 + kNumCfgs) * sizeof(unsigned) <= kCtrBytes, "counters fit");
+static_assert((2 + kNumCfgs) * sizeof(unsigned) <= kCtrBytes && 2 + kNumCfgs <= kTieCounter &&
+                  kCtrBytes == kCounterBlockBytes, "counters fit");
 
 size_t up16(size_t v) { return (v + 15) & ~(size_t)15; }
 
@@ -296,12 +297,12 @@ vdf::BatchParams plan_params(const vdf_plan *plan, void *ws, int g)
 
 int set_attributes()
 {
-    static std::once_flag once;
-    static cudaError_t err = cudaSuccess;
-    std::call_once(once, [] {
-        err = cudaFuncSetAttribute(vdf::batch_recheck_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)(vdf::kRecheckPerWarp * vdf::kRecheckWarps));
-        for (int c = 0; c < vdf::kNumCfgs && err == cudaSuccess; ++c) err = vdf::kGroupConfigure[c]();
+    static std::atomic<bool> done[vdf::kMaxDevices];
+    const cudaError_t err = vdf::once_per_device(done, [] {
+        cudaError_t e = cudaFuncSetAttribute(vdf::batch_recheck_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)(vdf::kRecheckPerWarp * vdf::kRecheckWarps));
+        for (int c = 0; c < vdf::kNumCfgs && e == cudaSuccess; ++c) e = vdf::kGroupConfigure[c]();
+        return e;
     });
     return err == cudaSuccess ? VDF_OK : VDF_E_CUDA;
 }
@@ -405,7 +406,7 @@ int vdf_filter_batch(vdf_plan *plan, void *workspace, size_t workspace_bytes, vo
     cudaStream_t st = (cudaStream_t)stream;
     const int sms = plan->sms;
     const int ngroups = (int)plan->groups.size();
-    cudaError_t e = cudaMemsetAsync(workspace, 0, (2 + ngroups) * sizeof(unsigned), st);
+    cudaError_t e = cudaMemsetAsync(workspace, 0, vdf::kCtrBytes, st);
     for (int g = 0; g < ngroups && e == cudaSuccess; ++g)
         e = vdf::kGroupLaunch[plan->groups[g].cfg](plan_params(plan, workspace, g), sms, st, plan->persistent.load());
     if (e == cudaSuccess) {

@@ -40,6 +40,10 @@ cudaError_t run_fp32_acw(const TileParams &prm, int R, int dist, int shape, cuda
 cudaError_t run_fp64_acw(const TileParams &prm, int R, int dist, cudaStream_t st);
 cudaError_t run_recheck_acw(const RecheckParams &prm, int R, int dist, int blocks, cudaStream_t st);
 
+// The argument checks of vdf_filter's FP32 path, except those of the workspace.
+int check_args_no_workspace(const uint8_t *img, int M, int N, int win, int filter, double p, int dist_mode,
+                            int minimax_q, const uint8_t *out, const int8_t *index_out);
+
 // FP32 pair terms of n pixel pairs (n x 6 ints), as the FP32 tile kernel computes them.
 cudaError_t run_debug_terms(const int *pairs, int n, int dist, int q, float *angle_out, float *l2_out,
                             cudaStream_t st);

@@ -11,7 +11,36 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <atomic>
+
 namespace vdf {
+
+// ------------------------------------------------- per-device set-up ----
+// Kernel attributes (the shared-memory opt-in) and device properties belong
+// to one device's context, so one-time set-up is tracked per device.
+constexpr int kMaxDevices = 64;
+
+// The current device, or -1 (no device, or an ordinal beyond kMaxDevices).
+inline int current_device()
+{
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return -1;
+    return dev;
+}
+
+// Runs set() once per device (again after a failure); `done` is a
+// zero-initialised static array.  Concurrent first calls may both run set(),
+// which must therefore be idempotent.
+template <class F>
+inline cudaError_t once_per_device(std::atomic<bool> (&done)[kMaxDevices], F set)
+{
+    const int dev = current_device();
+    if (dev < 0) return cudaErrorInvalidDevice;
+    if (done[dev].load(std::memory_order_acquire)) return cudaSuccess;
+    const cudaError_t e = set();
+    if (e == cudaSuccess) done[dev].store(true, std::memory_order_release);
+    return e;
+}
 
 enum Filter { BVDF = 0, DDF = 1, VMF = 2 };
 // Minkowski order of the distance term of Eq. (1) (DDF, VMF): 2, 1, or the
@@ -20,6 +49,14 @@ enum Norm { NL2 = 0, NL1 = 1, NLINF = 2 };
 enum Dist { EXACT = 0, MINIMAX = 1, RGB = 2 };
 
 // ------------------------------------------------------------- constants --
+
+// Counter block at the start of every FP32 workspace (256 bytes, 64 words):
+// word 0 = pixels listed for the FP64 recheck, word 1 = list overflow flag,
+// word kTieCounter = pixels whose near-minimal members the FP32 path proved
+// equal (structural ties, settled by the tie rule without a recheck).  The
+// batch path keeps its per-group work counters in words 2 .. 2 + groups.
+constexpr int kTieCounter = 63;
+constexpr size_t kCounterBlockBytes = 256;
 
 // Table 1, Section 2.1: minimax coefficients a_0..a_q for q = 2, 3, 4, padded
 // with zeros to degree 4 (a zero leading coefficient leaves Horner's rule

@@ -18,7 +18,10 @@
 //     library, until the process exits;
 //   - the first call on a device looks up the array's device address
 //     (cudaGetSymbolAddress, which may load this library's device code);
-//     make that first call before any stream capture;
+//     make that first call before any stream capture.  The address is kept
+//     per device for the life of the process: after cudaDeviceReset the
+//     kept address belongs to the destroyed context, so this entry point
+//     must not be used on that device again;
 //   - every call shares the one array and each call clears the counters it
 //     needs; calls that overlap on the GPU (different streams, or different
 //     host threads without ordering) race on it and must be serialised.
@@ -28,6 +31,7 @@
 #include <mutex>
 
 #include "../../include/vdf.h"
+#include "vdf_dispatch.h"
 
 namespace {
 
@@ -62,10 +66,12 @@ int scratch_address(void **addr)
 extern "C" int vdf_filter_noalloc(const uint8_t *img, int M, int N, int win, int filter, double p, int dist_mode,
                                   int minimax_q, uint8_t *out, int8_t *index_out, void *stream)
 {
-    if (M < 1 || N < 1) return VDF_E_INVALID;
+    // every argument check of vdf_filter first, then the capacity
+    int rc = vdf::check_args_no_workspace(img, M, N, win, filter, p, dist_mode, minimax_q, out, index_out);
+    if (rc != VDF_OK) return rc;
     if ((size_t)M * (size_t)N > kMaxPixels) return VDF_E_WORKSPACE;
     void *ws = nullptr;
-    int rc = scratch_address(&ws);
+    rc = scratch_address(&ws);
     if (rc != VDF_OK) return rc;
     rc = vdf_fp32_pass(img, M, N, win, filter, p, dist_mode, minimax_q, out, index_out, ws, kScratchBytes, stream);
     if (rc != VDF_OK) return rc;

@@ -701,7 +701,7 @@ __device__ __forceinline__ unsigned bit_mask(P pred)
 template <class C, class ZeroF, class WideF, class ArgF>
 __device__ __forceinline__ int resolve_near(unsigned near, const TileParams &prm, const typename C::Pix *pix,
                                             const unsigned *keys, int b, int ty, int tx, int gy, int gx, ZeroF zero,
-                                            WideF wide, ArgF argmin)
+                                            WideF wide, ArgF argmin, bool &tied)
 {
     constexpr int R = C::R, W = C::W, NW = C::NW, PXW = C::PXW;
     if (near == 0) near = 1u << C::CENTRE;   // not reached: the member attaining the minimum is near
@@ -747,7 +747,10 @@ __device__ __forceinline__ int resolve_near(unsigned near, const TileParams &prm
             if ((near >> k) & 1u) all_zero = all_zero && zero(k);
         equal = all_zero;
     }
-    if (equal) return ((near >> C::CENTRE) & 1u) ? C::CENTRE : first;
+    if (equal) {
+        tied = true;   // several near members, provably equal: a structural tie
+        return ((near >> C::CENTRE) & 1u) ? C::CENTRE : first;
+    }
     const unsigned mask = wide();
     const unsigned slot = atomicAdd(prm.recheck_ctr, 1u);
     if (slot < prm.recheck_cap)
@@ -790,7 +793,7 @@ __device__ __forceinline__ int acw_decide64(int sel_ddf, SF S, LF lc, PF px, int
 // slots (sum A, sum L2); P(k): shared-memory index of member k.
 template <class C, class PF>
 __device__ __forceinline__ int acw_select32(const TileParams &prm, const float4 *pix, const Aux *aux,
-                                            const unsigned *keys, const float2 *f, PF P, bool &unsure)
+                                            const unsigned *keys, const float2 *f, PF P, bool &unsure, bool &tied)
 {
     constexpr int R = C::R, W = C::W, NW = C::NW, CENTRE = C::CENTRE, DIST = C::DIST;
     (void)W;
@@ -803,7 +806,10 @@ __device__ __forceinline__ int acw_select32(const TileParams &prm, const float4 
 #pragma unroll
         for (int k = 0; k < NW; ++k)
             if ((near >> k) & 1u) same = same && keys[P(k)] == rkey;
-        if (same) return ((near >> CENTRE) & 1u) ? CENTRE : first;
+        if (same) {
+            tied = true;
+            return ((near >> CENTRE) & 1u) ? CENTRE : first;
+        }
         unsure = true;
         return argmin();
     };
@@ -825,7 +831,10 @@ __device__ __forceinline__ int acw_select32(const TileParams &prm, const float4 
 #pragma unroll
         for (int k = 0; k < NW; ++k)
             if ((near >> k) & 1u) zeros = zeros && v[k].x == 0.0f && v[k].y == 0.0f;
-        if (zeros && near) sel_ddf = ((near >> CENTRE) & 1u) ? CENTRE : __ffs(near) - 1;
+        if (zeros && near) {
+            tied = tied || (near & (near - 1)) != 0;
+            sel_ddf = ((near >> CENTRE) & 1u) ? CENTRE : __ffs(near) - 1;
+        }
         else
             sel_ddf = resolve(near, [&]() {
                 int arg = 0;
@@ -915,6 +924,7 @@ __device__ __forceinline__ void select_and_store(const TileParams &prm, int b, i
     const size_t lin = (size_t)gy * prm.N + gx;
     const auto *f = hw + tid * NW;
     int sel;
+    bool tied = false;   // FP32: settled by provable equality of the near members
     if constexpr (C::FP64 && C::ACW) {
         // ACWDDF: the DDF's choice, then the centre-weighted VMF levels and the switch
         const int sel_ddf = select64<DDF, NW>([&](int k) { return f[k].x; });
@@ -931,7 +941,8 @@ __device__ __forceinline__ void select_and_store(const TileParams &prm, int b, i
     } else if constexpr (C::ACW) {
         bool unsure = false;
         sel = acw_select32<C>(prm, pix, aux, keys, f,
-                              [&](int k) { return (ty + k / W) * PXW + (tx + k % W) + 2 * R; }, unsure);
+                              [&](int k) { return (ty + k / W) * PXW + (tx + k % W) + 2 * R; }, unsure, tied);
+        tied = tied && !unsure;
         if (unsure) {
             // the FP64 recheck decides the whole of Eq. (9) (every member)
             constexpr unsigned ALL = (1u << NW) - 1u;
@@ -1024,7 +1035,8 @@ __device__ __forceinline__ void select_and_store(const TileParams &prm, int b, i
                             arg = k;
                         }
                     return arg;
-                });
+                },
+                tied);
         } else {
             // general bounds (Method 1, and DDF with p not a multiple of 1/4):
             // the n scores (f, E) of the window, in registers
@@ -1070,8 +1082,15 @@ __device__ __forceinline__ void select_and_store(const TileParams &prm, int b, i
                             arg = k;
                         }
                     return arg;
-                });
+                },
+                tied);
         }
+    }
+    if constexpr (!C::FP64) {
+        // structural ties of this warp's pixels, one atomic per warp
+        const unsigned act = __activemask();
+        const unsigned m = __ballot_sync(act, tied);
+        if (m && (threadIdx.x & 31) == __ffs(act) - 1) atomicAdd(prm.recheck_ctr + kTieCounter, (unsigned)__popc(m));
     }
     const Pix v = pix[(ty + sel / W) * PXW + (tx + sel % W) + 2 * R];
     if constexpr (C::F32IN) {
@@ -1215,13 +1234,12 @@ __global__ void __launch_bounds__(C::NT, C::MINB) tile_kernel(const TileParams p
 template <class C>
 cudaError_t launch_tile(const TileParams &prm, cudaStream_t st)
 {
-    // set once per instantiation; concurrent first calls may both set it (idempotent)
-    static std::atomic<bool> configured{false};
-    if (!configured.load(std::memory_order_acquire)) {
-        cudaError_t e = cudaFuncSetAttribute(tile_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
-        if (e != cudaSuccess) return e;
-        configured.store(true, std::memory_order_release);
-    }
+    // set once per instantiation and device
+    static std::atomic<bool> configured[kMaxDevices];
+    cudaError_t e = once_per_device(configured, [] {
+        return cudaFuncSetAttribute(tile_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+    });
+    if (e != cudaSuccess) return e;
     dim3 grid((prm.N + C::TW - 1) / C::TW, (prm.M + C::TH - 1) / C::TH, prm.B);
     tile_kernel<C><<<grid, C::NT, C::SMEM, st>>>(prm);
     return cudaGetLastError();
@@ -1404,13 +1422,12 @@ template <int R, int FILTER, int DIST, bool F32IN = false, int NORM = NL2, bool 
 cudaError_t launch_recheck(const RecheckParams &prm, int blocks, cudaStream_t st)
 {
     using C = RecheckCfg<R, FILTER, DIST>;
-    static std::atomic<bool> configured{false};
-    if (!configured.load(std::memory_order_acquire)) {
-        cudaError_t e = cudaFuncSetAttribute(recheck_kernel<R, FILTER, DIST, F32IN, NORM, ACW>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
-        if (e != cudaSuccess) return e;
-        configured.store(true, std::memory_order_release);
-    }
+    static std::atomic<bool> configured[kMaxDevices];
+    cudaError_t e = once_per_device(configured, [] {
+        return cudaFuncSetAttribute(recheck_kernel<R, FILTER, DIST, F32IN, NORM, ACW>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+    });
+    if (e != cudaSuccess) return e;
     recheck_kernel<R, FILTER, DIST, F32IN, NORM, ACW><<<blocks, 32 * C::WARPS, C::SMEM, st>>>(prm);
     return cudaGetLastError();
 }

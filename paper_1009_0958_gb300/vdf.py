@@ -51,6 +51,7 @@ def lib():
             L.vdf_fp32_pass.argtypes = [P, i, i, i, i, d, i, i, P, P, P, sz, P]
             L.vdf_fp64_recheck.argtypes = [P, i, i, i, i, d, i, i, P, P, P, sz, P]
             L.vdf_workspace_stats.argtypes = [P, P, P, P]
+            L.vdf_read_stats.argtypes = [P, P, P]
             L.vdf_debug_fp32_scores.argtypes = [P, i, i, i, i, d, i, i, P, P]
             L.vdf_debug_fp32_terms.argtypes = [P, i, i, i, P, P, P]
             L.vdf_debug_fp32_terms_f32.argtypes = [P, i, P, P, P]
@@ -165,6 +166,20 @@ def workspace_stats(workspace: torch.Tensor, stream=None):
     wp, _ = _aligned(workspace)
     _check(lib().vdf_workspace_stats(wp, ctypes.byref(r), ctypes.byref(o), _stream(stream)))
     return int(r.value), int(o.value)
+
+
+class Stats(ctypes.Structure):
+    """vdf_stats of vdf.h."""
+    _fields_ = [("rechecked", ctypes.c_int64), ("structural_ties", ctypes.c_int64), ("overflow", ctypes.c_int32)]
+
+
+def read_stats(workspace: torch.Tensor, stream=None) -> dict:
+    """Counters of the last FP32 call using ``workspace``: pixels rechecked in
+    FP64, pixels settled as structural ties, overflow flag."""
+    st = Stats()
+    wp, _ = _aligned(workspace)
+    _check(lib().vdf_read_stats(wp, ctypes.byref(st), _stream(stream)))
+    return {"rechecked": int(st.rechecked), "structural_ties": int(st.structural_ties), "overflow": int(st.overflow)}
 
 
 def host_buffer_bytes(M: int, N: int, precision="fp32") -> int:

@@ -16,6 +16,33 @@ def L():
     return vdf.lib()
 
 
+@pytest.fixture(scope="module")
+def B():
+    """Two 1 MiB buffers for calls that must fail their host-side checks.  On a
+    machine with a GPU they are device memory, so a check that regressed and
+    let a call through would launch on valid memory; without a GPU they are
+    host memory (nothing can be launched there)."""
+    import numpy as np
+    import torch
+    if torch.cuda.is_available():
+        keep = [torch.zeros(1 << 20, dtype=torch.uint8, device="cuda") for _ in range(2)]
+        ptrs = [t.data_ptr() for t in keep]
+    else:
+        keep = [np.zeros(1 << 20, np.uint8) for _ in range(2)]
+        ptrs = [a.ctypes.data for a in keep]
+    yield [ctypes.c_void_p(v) for v in ptrs]
+    del keep
+
+
+@pytest.fixture(scope="module")
+def H():
+    """A 1 MiB host buffer (host frame arguments)."""
+    import numpy as np
+    a = np.zeros(1 << 20, np.uint8)
+    yield ctypes.c_void_p(a.ctypes.data)
+    del a
+
+
 def declared_functions():
     text = open(os.path.join(ROOT, "include", "vdf.h")).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
@@ -43,19 +70,18 @@ def test_strerror_and_sizes(L):
     dict(filter=1, p=1.5), dict(filter=1, p=-0.1),
     dict(dist=3), dict(dist=1, q=5), dict(precision=2),
 ])
-def test_invalid_arguments_rejected_on_host(L, args):
-    a = dict(img=ctypes.c_void_p(0x10000), M=8, N=8, win=3, filter=0, p=0.5, dist=0, q=4, precision=0,
-             out=ctypes.c_void_p(0x20000))
+def test_invalid_arguments_rejected_on_host(L, B, args):
+    a = dict(img=B[0], M=8, N=8, win=3, filter=0, p=0.5, dist=0, q=4, precision=0, out=B[1])
     a.update(args)
     rc = L.vdf_filter(a["img"], a["M"], a["N"], a["win"], a["filter"], a["p"], a["dist"], a["q"], a["precision"],
                       a["out"], None, None, None, 0, None)
     assert rc == -1
 
 
-def test_minkowski_order_checked_on_host(L):
+def test_minkowski_order_checked_on_host(L, B):
     """vdf_filter_lp: orders 1, 2 and infinity (0) only; the DDF at order 1 or
     infinity needs the exact angle; the VMF ignores p and dist_mode."""
-    img, out = ctypes.c_void_p(0x10000), ctypes.c_void_p(0x20000)
+    img, out = B
 
     def call(filter, p, order, dist, precision=0, M=8):
         return L.vdf_filter_lp(img, M, 8, 3, filter, p, order, dist, 4, precision, out, None, None, None, 0, None)
@@ -70,9 +96,9 @@ def test_minkowski_order_checked_on_host(L):
     assert f32 == -6                                     # no VMF on the float path
 
 
-def test_acwddf_arguments_checked_on_host(L):
+def test_acwddf_arguments_checked_on_host(L, B):
     """vdf_filter_acwddf: lambda in [1, d - 2], finite T, the usual checks."""
-    img, out = ctypes.c_void_p(0x10000), ctypes.c_void_p(0x20000)
+    img, out = B
 
     def call(win, lam, T, dist=0, q=4, precision=0):
         return L.vdf_filter_acwddf(img, 8, 8, win, dist, q, lam, T, precision, out, None, None, 0, None)
@@ -82,14 +108,14 @@ def test_acwddf_arguments_checked_on_host(L):
     assert call(3, 2, 10.8, precision=1) == -5    # valid, but no workspace
 
 
-def test_aliasing_and_workspace_checks(L):
-    p = ctypes.c_void_p(0x10000)
+def test_aliasing_and_workspace_checks(L, B):
+    p = B[0]
     assert L.vdf_filter(p, 8, 8, 3, 0, 0.5, 0, 4, 0, p, None, None, None, 0, None) == -1      # out == img
-    assert L.vdf_filter(p, 8, 8, 3, 0, 0.5, 0, 4, 1, ctypes.c_void_p(0x20000), None, None, None, 0, None) == -5
+    assert L.vdf_filter(p, 8, 8, 3, 0, 0.5, 0, 4, 1, B[1], None, None, None, 0, None) == -5
 
 
-def test_debug_terms_arguments_checked_on_host(L):
-    p = ctypes.c_void_p(0x10000)
+def test_debug_terms_arguments_checked_on_host(L, B):
+    p = B[0]
     assert L.vdf_debug_fp32_terms(None, 4, 0, 4, None, None, None) == -1
     assert L.vdf_debug_fp32_terms(p, -1, 0, 4, None, None, None) == -1
     assert L.vdf_debug_fp32_terms(p, 4, 3, 4, None, None, None) == -1
@@ -97,9 +123,9 @@ def test_debug_terms_arguments_checked_on_host(L):
     assert L.vdf_debug_fp32_terms(p, 0, 0, 4, None, None, None) == 0    # nothing to launch
 
 
-def test_host_frames_arguments_checked_on_host(L):
-    p = ctypes.c_void_p(0x10000)
-    arr = (ctypes.c_void_p * 1)(p)
+def test_host_frames_arguments_checked_on_host(L, B, H):
+    p = B[0]
+    arr = (ctypes.c_void_p * 1)(H)
     nul = (ctypes.c_void_p * 1)(None)
     assert L.vdf_filter_host_frames(None, arr, None, 1, 8, 8, 3, 0, 0.5, 0, 4, 1, p, 1 << 20, None) == -1
     assert L.vdf_filter_host_frames(arr, nul, None, 1, 8, 8, 3, 0, 0.5, 0, 4, 1, p, 1 << 20, None) == -1
@@ -111,9 +137,9 @@ def test_host_frames_arguments_checked_on_host(L):
     assert L.vdf_host_frames_buffer_bytes(8, 8, 1) == 3 * ((one + 255) // 256 * 256)
 
 
-def test_float_debug_entries_checked_on_host(L):
+def test_float_debug_entries_checked_on_host(L, B):
     assert L.vdf_debug_fp32_terms_f32(None, 4, None, None, None) == -1
-    assert L.vdf_debug_fp32_terms_f32(ctypes.c_void_p(0x10000), -1, None, None, None) == -1
+    assert L.vdf_debug_fp32_terms_f32(B[0], -1, None, None, None) == -1
     assert L.vdf_debug_sqrt_error(None, None) == -1
 
 

@@ -40,8 +40,20 @@ def test_noalloc_equals_workspace_path_on_consecutive_calls(V, win, filter, p):
 
 
 def test_noalloc_rejects_images_above_capacity(V):
+    """An image one row above the limit gets VDF_E_WORKSPACE.  Its buffers are
+    real device memory of the full size, so even a size check that regressed
+    would filter valid memory instead of faulting."""
+    M, N = 2049, 1024
+    assert V.NOALLOC_MAX_PIXELS < M * N
     L = V.lib()
     V.filter_noalloc(torch.zeros((4, 4, 3), dtype=torch.uint8, device="cuda"))   # sets argtypes
-    rc = L.vdf_filter_noalloc(ctypes.c_void_p(0x1000), 2049, 1024, 3, 0, 0.5, 0, 4, ctypes.c_void_p(0x9000000), None,
-                              None)
-    assert rc == -5 and V.NOALLOC_MAX_PIXELS < 2049 * 1024
+    img = torch.zeros((M, N, 3), dtype=torch.uint8, device="cuda")
+    out = torch.empty_like(img)
+    idx = torch.empty((M, N), dtype=torch.int8, device="cuda")
+    rc = L.vdf_filter_noalloc(ctypes.c_void_p(img.data_ptr()), M, N, 3, 0, 0.5, 0, 4, ctypes.c_void_p(out.data_ptr()),
+                              ctypes.c_void_p(idx.data_ptr()), None)
+    torch.cuda.synchronize()
+    assert rc == -5
+    # argument errors come before the size check
+    rc = L.vdf_filter_noalloc(None, M, N, 3, 0, 0.5, 0, 4, ctypes.c_void_p(out.data_ptr()), None, None)
+    assert rc == -1
