@@ -44,6 +44,11 @@ CONFIG = {"workload": WORKLOAD, "M": M, "N": N, "win": WIN, "filter": FILTER, "p
 
 
 
+def set_workload(m, n, noise, nframes, workload, metric, config):
+    global M, N, NOISE, FRAMES, WORKLOAD, METRIC, CONFIG
+    M, N, NOISE, FRAMES, WORKLOAD, METRIC, CONFIG = m, n, noise, nframes, workload, metric, config
+
+
 def use_4k_workload():
     """The precision stress case (3840 x 2160, 20% impulsive noise): same
     filter and path, frames rebound for every function of this module."""
@@ -57,28 +62,54 @@ def use_4k_workload():
               "l2": "inputs larger than L2: 6 distinct frames (149 MB) in rotation"}
 
 
-# FP32-pipe lane operations per output pixel of the FP32 tile kernel for this
-# workload, counted from the source (see the design notes): 40 unique pair
-# terms x 30 ops, separable window sums 2 x 305 adds, 25 DDF scores x 15 ops
-# (log2 range reduction, combine, bound), selection 25 x 6 ops.
-ALU_OPS_PER_PIXEL = 40 * 30 + 2 * 305 + 25 * 15 + 25 * 6
+# Algorithmic work per output pixel (the roofline's numerator), fixed before
+# any tuning from the operation counts of the method itself, not from the
+# kernels' source: see opcount().
+ANGLE_TERM_OPS = {"exact": 25, "minimax": 25, "rgb": 9}
+DIST_TERM_OPS = {2: 7, 1: 6, "inf": 6}
 
 
-def ops_per_pixel(win: int, filt: str) -> int:
-    """The same source-level count for any window and filter: U = ((2w-1)^2-1)/2
-    pair terms of 30 ops (DDF: angle + L2) or 24 (BVDF: angle); per
-    aggregate component (2 for DDF) (2w-1) w (w-1) row-sum adds plus w^3
-    accumulator adds; per member 15 score ops (DDF) or 2 (BVDF) and 6
-    selection ops.  ops_per_pixel(5, "ddf") == ALU_OPS_PER_PIXEL.  VMF (Eq. (1)):
-    6 ops per pair term (three component differences and their combination),
-    one aggregate component, 2 score ops per member."""
+def opcount(win: int, filt: str, dist: str = "exact", order=2) -> int:
+    """FP32-pipe operations per output pixel of one filter configuration.
+
+    Derivation (window side w, n = w^2 members, U = ((2w-1)^2 - 1) / 2
+    unordered pair offsets a pixel meets across the windows that contain it,
+    12 for 3x3 and 40 for 5x5):
+      * pair terms, each computed once and reused by every window holding the
+        pair: U x (angle + distance).  The angle of Eq. (2) (or Method 1's
+        polynomial): 3 multiply-adds for <x,y>, 6 for |x cross y|^2, 2 SFU
+        operations, 8 polynomial multiply-adds, 1 select, rounded to 25.
+        Method 2's chromaticity distance (Eq. (7)): 8 multiply-adds + 1 SFU = 9.
+        The Minkowski distance of Eq. (1): order 2, 6 multiply-adds + 1 SFU
+        = 7; orders 1 and infinity, 3 differences + 3 combines = 6.
+      * aggregation: n (n - 1) adds (each of the n members sums n terms);
+      * selection: n - 1 compares;
+      * DDF combine: 2 n logarithms (one per aggregate).
+    BVDF = U x angle + n(n-1) + (n-1); DDF adds U x distance and 2n; VMF =
+    U x distance + n(n-1) + (n-1).  DDF 5x5 exact: 40 x 32 + 600 + 24 + 50 =
+    1954.  The count does not depend on the kernels, so it does not move when
+    they change; a kernel that needs fewer operations shows as a higher
+    fraction of the peak.
+    """
     U, n = ((2 * win - 1) ** 2 - 1) // 2, win * win
-    sums = (2 * win - 1) * win * (win - 1) + win ** 3
-    if filt == "ddf":
-        return U * 30 + 2 * sums + n * 15 + n * 6
+    agg, sel = n * (n - 1), n - 1
     if filt == "vmf":
-        return U * 6 + sums + n * 2 + n * 6
-    return U * 24 + sums + n * 2 + n * 6
+        return U * DIST_TERM_OPS[order] + agg + sel
+    if filt == "bvdf":
+        return U * ANGLE_TERM_OPS[dist] + agg + sel
+    return U * (ANGLE_TERM_OPS[dist] + DIST_TERM_OPS[order]) + agg + sel + 2 * n
+
+
+def opcount_acwddf(win: int, dist: str = "exact") -> int:
+    """The ACWDDF of Eq. (9): the DDF's count, plus n centre distances (order
+    2), three centre-weighted levels of n multiply-adds and n - 1 compares each,
+    and the switching sum over three levels (one angle, one distance and two
+    operations each)."""
+    n = win * win
+    return (opcount(win, "ddf", dist) + n * DIST_TERM_OPS[2] + 3 * (n + n - 1)
+            + 3 * (ANGLE_TERM_OPS[dist] + DIST_TERM_OPS[2] + 2))
+
+
 SMS, FP32_LANES_PER_SM = 152, 128
 
 # DRAM bytes per launch of the FP32 tile kernel, from one ncu capture, keyed
@@ -88,8 +119,8 @@ TRAFFIC_BY_SOURCE = {"68d1641ecb2a01ef": 6296320}   # profiles/tile_kernel_fp32_
 
 # DRAM bytes per launch of the backward gather on the differentiable workload
 # (profiles/backward_gather_autograd_32x512x512.md), keyed like the above by a
-# hash of vdf_backward.cu.
-BACKWARD_TRAFFIC_BY_SOURCE = {"68d1641ecb2a01ef": 6296320}
+# hash of vdf_backward.cu only.
+BACKWARD_TRAFFIC_BY_SOURCE = {}
 
 
 def backward_source_hash() -> str:
@@ -153,8 +184,9 @@ class ClockSampler:
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
          "clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: int):
+    def __init__(self, gpu_index: int, interval_ms: int = 20):
         self.gpu = gpu_index
+        self.interval = interval_ms
         self.proc = None
         self.path = None
 
@@ -164,7 +196,7 @@ class ClockSampler:
         try:
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", str(self.interval)],
                                          stdout=self.fh, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
@@ -191,6 +223,8 @@ class ClockSampler:
         os.unlink(self.path)
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        # samples taken while the GPU was busy: power well above idle, or the
+        # SM clock at least half of its maximum
         sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
         mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
@@ -312,13 +346,13 @@ def run_vmf_workload(args):
                                   "fp64_value": M * N / (ms64 * 1e-3) / 1e6, "speedup_vs_fp64": ms64 / ms,
                                   "rechecked_last_frame": rechecked}
     head = orders["2"]
-    ops = ops_per_pixel(WIN, "vmf")
+    ops = opcount(WIN, "vmf")
     achieved = ops * M * N / (head["ms_per_step"] * 1e-3) / 1e12
     peak = SMS * FP32_LANES_PER_SM * 2.070e9 / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "T FP32-pipe ops/s",
                 "frac": achieved / peak, "traffic": None,
                 "kernel": "vdf::tile_kernel<R=2,VMF,order 2,FP32> (the whole call: counter reset, tile kernel, "
-                          "recheck)", "ops_per_pixel": ops,
+                          "recheck)", "ops_per_pixel": ops, "ops_basis": "opcount(5, 'vmf'): algorithmic count",
                 "peak_basis": "152 SMs x 128 FP32 lanes x 2070 MHz max SM clock"}
     line = {"metric": "Mpix/s, 5x5 VMF (Eq. (1), Minkowski order 2) on 1080p RGB: FP32+FP64-tie path",
             "value": head["value"], "unit": UNIT, "n_gpus": 1, "steps": K, "warmup": args.warmup,
@@ -379,13 +413,13 @@ def run_acwddf_workload(args):
                                             "fp64_value": M * N / (ms64 * 1e-3) / 1e6,
                                             "speedup_vs_fp64": ms64 / ms, "rechecked_last_frame": rechecked}
     head = cases["3x3 exact"]
-    ops = ops_per_pixel(3, "ddf")
+    ops = opcount_acwddf(3)
     achieved = ops * M * N / (head["ms_per_step"] * 1e-3) / 1e12
     peak = SMS * FP32_LANES_PER_SM * 2.070e9 / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "T FP32-pipe ops/s",
                 "frac": achieved / peak, "traffic": None,
                 "kernel": "vdf::tile_kernel<R=1,DDF,EXACT,FP32,ACW> (the whole call: counter reset, tile kernel, "
-                          "recheck); ops of the DDF only (the CWVMF levels and the switch not counted)",
+                          "recheck); ops: opcount_acwddf(3), the DDF, the CWVMF levels and the switch",
                 "ops_per_pixel": ops, "peak_basis": "152 SMs x 128 FP32 lanes x 2070 MHz max SM clock"}
     line = {"metric": "Mpix/s, 3x3 ACWDDF (Eq. (9), lambda 2, T 10.8) on 1080p RGB: FP32+FP64-tie path",
             "value": head["value"], "unit": UNIT, "n_gpus": 1, "steps": K, "warmup": args.warmup,
@@ -400,9 +434,10 @@ def run_acwddf_workload(args):
     print(json.dumps(line), flush=True)
 
 
-def run_batch_workload(args):
+def run_batch_workload(args, emit: bool = True):
     """256 uneven images, mixed 3x3/5x5 BVDF/DDF, one persistent launch per
-    batch replayed from a CUDA graph, tile shapes from the autotuner."""
+    batch replayed from a CUDA graph, tile shapes from the autotuner.  Returns
+    the JSON line (printed when ``emit``)."""
     import torch
 
     from paper_1009_0958_gb300 import build as vbuild
@@ -434,6 +469,7 @@ def run_batch_workload(args):
         torch.cuda.synchronize(dev)
     ms = e0.elapsed_time(e1) / K
     rechecked, overflow = plan.stats()
+    ties = vdf.read_stats(plan.workspace)["structural_ties"]
     groups = len(set(cfgs))
     # the persistent work-queue form of the same plan, timed beside it
     plan_p = vdf.Plan(items, persistent=True)
@@ -448,13 +484,14 @@ def run_batch_workload(args):
     torch.cuda.synchronize(dev)
     ms_p = e0.elapsed_time(e1) / Kp
     plan_p.close()
-    ops = sum(ops_per_pixel(w, f) * int(x.shape[0]) * int(x.shape[1]) for x, (w, f) in zip(imgs, cfgs))
+    ops = sum(opcount(w, f) * int(x.shape[0]) * int(x.shape[1]) for x, (w, f) in zip(imgs, cfgs))
     achieved = ops / (ms * 1e-3) / 1e12
     peak = SMS * FP32_LANES_PER_SM * 2.070e9 / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "T FP32-pipe ops/s",
                 "frac": achieved / peak, "traffic": None,
                 "kernel": "vdf::batch_item_kernel (the step's time, which also holds the batch recheck kernel)",
-                "ops_per_step": ops, "peak_basis": "152 SMs x 128 FP32 lanes x 2070 MHz max SM clock"}
+                "ops_per_step": ops, "ops_basis": "sum over the images of opcount(win, filter) x pixels",
+                "peak_basis": "152 SMs x 128 FP32 lanes x 2070 MHz max SM clock"}
     line = {"metric": "Mpix/s, batch of 256 uneven RGB images, mixed 3x3/5x5 BVDF/DDF, FP32+FP64-tie path",
             "value": pixels / (ms * 1e-3) / 1e6, "unit": UNIT, "n_gpus": 1, "steps": K, "warmup": args.warmup,
             "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -467,12 +504,14 @@ def run_batch_workload(args):
             "persistent_form": {"value": pixels / (ms_p * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": ms_p,
                                 "steps": Kp, "launch": "the same plan with persistent tile kernels (CTAs take "
                                                        "work items from an atomic counter)"},
-            "recheck_fraction": rechecked / pixels, "overflow": overflow, "gpu_launches": (groups + 1) * K,
-            "roofline": roofline, "clocks": clk.summary()}
-    print(json.dumps(line), flush=True)
+            "recheck_fraction": rechecked / pixels, "structural_tie_fraction": ties / pixels, "overflow": overflow,
+            "gpu_launches": (groups + 1) * K, "roofline": roofline, "clocks": clk.summary()}
+    if emit:
+        print(json.dumps(line), flush=True)
+    return line
 
 
-def run_autograd_workload(args):
+def run_autograd_workload(args, emit: bool = True):
     """The differentiable workload: DDF 3x3 (p = 0.25) forward on a float32
     32 x 3 x 512 x 512 batch in [0, 1] (the FP32 certified path for float
     input, with its FP64 recheck) plus the gather-form backward; the backward
@@ -521,6 +560,7 @@ def run_autograd_workload(args):
     fwd64 = e0.elapsed_time(e1) / 3
     px = B * Mf * Nf
     bw = 25.0 * px / (bwd * 1e-3) / 1e9   # grad_y 12 B + index 1 B + grad_x 12 B per pixel
+    hbm = measured_peaks().get("hbm_gbs") or 6800.0
     line = {"metric": "Mpix/s, DDF 3x3 forward + backward on float32 32x3x512x512 (differentiable path)",
             "value": px / ((fwd + bwd) * 1e-3) / 1e6, "unit": UNIT, "n_gpus": 1, "steps": K,
             "warmup": args.warmup, "ms_per_step": fwd + bwd, "higher_is_better": True, "scaling": "weak",
@@ -530,11 +570,156 @@ def run_autograd_workload(args):
             "forward_ms": fwd, "backward_ms": bwd, "forward_fp64_ms": fwd64,
             "forward_recheck_fraction": rechecked / px,
             "roofline": {"bound": "hbm", "kernel": "vdf::backward_gather<R=1>", "achieved": bw,
-                         "peak": 6793.1, "unit": "GB/s", "frac": bw / 6793.1,
+                         "peak": hbm, "unit": "GB/s", "frac": bw / hbm,
+                         "peak_basis": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
                          "traffic": BACKWARD_TRAFFIC_BY_SOURCE.get(backward_source_hash()),
                          "algorithmic_bytes_per_pixel": 25},
             "gpu_launches": 2 * K, "clocks": clk.summary()}
-    print(json.dumps(line), flush=True)
+    if emit:
+        print(json.dumps(line), flush=True)
+    return line
+
+
+def measure_frames(L, vdf, torch, dev, sp, stream, Mh, Nh, noise, nframes, seed0, K, warmup, shape_arg, K64,
+                   ws, e2e_frames=0):
+    """The FP32 certified step on ``nframes`` distinct Mh x Nh frames in
+    rotation (the FP64 recheck of frame i on a second stream, three
+    workspaces), then, untimed, its recheck and structural-tie counts per
+    frame; the plain FP64 path on the first K64 frames; every pixel of those
+    frames compared between the two precisions; optionally the end-to-end
+    host-frame call over ``e2e_frames`` frames.  Times are max over ranks."""
+    from paper_1009_0958_gb300 import synth
+    host_frames = [synth.make_image(Mh, Nh, seed0 + i, noise, rectangles=RECTS)[1] for i in range(nframes)]
+    ins = [torch.from_numpy(f).to(dev) for f in host_frames]
+    outs = [torch.empty_like(x) for x in ins]
+    idxs = [torch.empty((Mh, Nh), dtype=torch.int8, device=dev) for _ in ins]
+    wsb = vdf.workspace_bytes(Mh, Nh, "fp32")
+    wst = [torch.empty(wsb + 256, dtype=torch.uint8, device=dev) for _ in range(3)]
+    wsp = [vdf._aligned(w) for w in wst]
+    side = torch.cuda.Stream(dev)
+    sp2 = ctypes.c_void_p(side.cuda_stream)
+    VP = ctypes.c_void_p
+
+    def check(rc):
+        if rc != 0:
+            raise RuntimeError(f"libvdf: {L.vdf_strerror(rc).decode()} {L.vdf_last_cuda_error().decode()}")
+
+    def fp32_pass(x, o, ix, w=0):
+        return L.vdf_fp32_pass(VP(x.data_ptr()), Mh, Nh, WIN, 1, P, 0, Q, VP(o.data_ptr()), VP(ix.data_ptr()),
+                               wsp[w][0], wsp[w][1], sp)
+
+    def recheck(x, o, ix, w=0, on_side=False):
+        return L.vdf_fp64_recheck(VP(x.data_ptr()), Mh, Nh, WIN, 1, P, 0, Q, VP(o.data_ptr()), VP(ix.data_ptr()),
+                                  wsp[w][0], wsp[w][1], sp2 if on_side else sp)
+
+    def fp64_step(i):
+        return L.vdf_filter(VP(ins[i].data_ptr()), Mh, Nh, WIN, 1, P, 0, Q, 0, VP(outs[i].data_ptr()),
+                            VP(idxs[i].data_ptr()), None, None, 0, sp)
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+
+    if shape_arg is None:
+        shape, _ = vdf.autotune(ins[0], WIN, FILTER, P, DIST, Q, reps=5)
+    else:
+        shape = shape_arg
+        vdf.set_tuned_shape(WIN, FILTER, DIST, shape)
+    tw, th = vdf.tile_shapes()[shape]
+    for s in range(warmup):
+        i = s % nframes
+        check(fp32_pass(ins[i], outs[i], idxs[i]))
+        check(recheck(ins[i], outs[i], idxs[i]))
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    t_wall = time.perf_counter()
+    t_start.record(stream)
+    for s in range(K):
+        i, w = s % nframes, s % 3
+        if s >= 3:
+            stream.wait_event(ev[s - 3][2])    # workspace w is free again
+        ev[s][0].record(stream)
+        check(fp32_pass(ins[i], outs[i], idxs[i], w))
+        ev[s][1].record(stream)
+        side.wait_event(ev[s][1])
+        check(recheck(ins[i], outs[i], idxs[i], w, on_side=True))
+        ev[s][2].record(side)
+    stream.wait_event(ev[K - 1][2])
+    t_end.record(stream)
+    barrier()
+    t_wall = time.perf_counter() - t_wall
+    kernel_ms = [a.elapsed_time(b) for a, b, _ in ev]
+    step_ms = [a.elapsed_time(c) for a, _, c in ev]
+    total_ms = reduce_max(t_start.elapsed_time(t_end), ws, dev)
+
+    # untimed: the FP32 path once more on the first frames (into spare
+    # buffers), its counters per frame
+    o32 = [torch.empty_like(ins[0]) for _ in range(K64)]
+    i32 = [torch.empty_like(idxs[0]) for _ in range(K64)]
+    rechecked, ties = [], []
+    for i in range(min(nframes, K)):
+        if i < K64:
+            o, ix = o32[i], i32[i]
+        else:
+            o, ix = outs[i], idxs[i]
+        check(fp32_pass(ins[i], o, ix))
+        check(recheck(ins[i], o, ix))
+        st = vdf.read_stats(wst[0])
+        rechecked.append(st["rechecked"])
+        ties.append(st["structural_ties"])
+
+    # the plain FP64 GPU path (the metric's denominator)
+    for s in range(3):
+        check(fp64_step(s % nframes))
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for s in range(K64):
+        check(fp64_step(s % nframes))
+    e1.record(stream)
+    barrier()
+    fp64_ms = reduce_max(e0.elapsed_time(e1), ws, dev) / K64
+
+    # every pixel of the frames both paths filtered: member index and RGB
+    mism = 0
+    for i in range(min(K64, nframes, K)):
+        bad = (i32[i] != idxs[i]) | (o32[i] != outs[i]).any(dim=2)
+        mism += int(bad.sum().item())
+    compared = min(K64, nframes, K)
+
+    res = {"total_ms": total_ms, "K": K, "kernel_ms": statistics.mean(kernel_ms),
+           "step_ms_mean": statistics.mean(step_ms), "wall_s": t_wall, "shape": (tw, th),
+           "fp64_ms": fp64_ms, "K64": K64,
+           "recheck_fraction": float(np.mean(rechecked)) / (Mh * Nh) if rechecked else None,
+           "structural_tie_fraction": float(np.mean(ties)) / (Mh * Nh) if ties else None,
+           "mismatches_vs_fp64": mism, "frames_compared": compared}
+
+    if e2e_frames:
+        # vdf_filter_host_frames: frames from pinned host memory to pinned
+        # host memory in one call; every frame's upload and download is inside
+        # the timed region, overlapped with the filtering of its neighbours
+        pin_in = [torch.from_numpy(f).pin_memory() for f in host_frames[:4]]
+        pin_out = [torch.empty((Mh, Nh, 3), dtype=torch.uint8).pin_memory() for _ in range(2)]
+        pin_idx = [torch.empty((Mh, Nh), dtype=torch.int8).pin_memory() for _ in range(2)]
+        dbuf = torch.empty(vdf.host_frames_buffer_bytes(Mh, Nh, "fp32") + 256, dtype=torch.uint8, device=dev)
+        bp, bl = vdf._aligned(dbuf)
+
+        def e2e_call(count):
+            a = (VP * count)(*[pin_in[s % 4].data_ptr() for s in range(count)])
+            b = (VP * count)(*[pin_out[s % 2].data_ptr() for s in range(count)])
+            c = (VP * count)(*[pin_idx[s % 2].data_ptr() for s in range(count)])
+            return L.vdf_filter_host_frames(a, b, c, count, Mh, Nh, WIN, 1, P, 0, Q, 1, bp, bl, sp)
+        check(e2e_call(3))
+        barrier()
+        t0 = time.perf_counter()
+        check(e2e_call(e2e_frames))
+        barrier()
+        res["e2e_s"] = reduce_max(time.perf_counter() - t0, ws, dev)
+        res["e2e_frames"] = e2e_frames
+    return res
 
 
 def main():
@@ -544,6 +729,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the 4K, batch and differentiable results added to the headline line")
     ap.add_argument("--fp64-steps", type=int, default=None)
     ap.add_argument("--workload", default="ddf5_1080p",
                     choices=["ddf5_1080p", "ddf5_4k", "batch", "autograd", "vmf5_1080p", "acwddf_1080p"])
@@ -578,140 +765,66 @@ def main():
     L = vdf.lib()
     stream = torch.cuda.current_stream(dev)
     sp = ctypes.c_void_p(stream.cuda_stream)
-
-    host_frames = frames(FRAMES, seed0=frame_seed(rank))
-    ins = [torch.from_numpy(f).to(dev) for f in host_frames]
-    outs = [torch.empty_like(x) for x in ins]
-    idxs = [torch.empty((M, N), dtype=torch.int8, device=dev) for _ in ins]
-    wsb = vdf.workspace_bytes(M, N, "fp32")
-    # three workspaces: the FP64 recheck of frame i (second stream) overlaps
-    # the FP32 passes of frames i+1 and i+2
-    wst = [torch.empty(wsb + 256, dtype=torch.uint8, device=dev) for _ in range(3)]
-    wsp = [vdf._aligned(w) for w in wst]
-    side = torch.cuda.Stream(dev)
-    sp2 = ctypes.c_void_p(side.cuda_stream)
-
-    def fp32_pass(i, w=0):
-        return L.vdf_fp32_pass(ctypes.c_void_p(ins[i].data_ptr()), M, N, WIN, 1, P, 0, Q,
-                               ctypes.c_void_p(outs[i].data_ptr()), ctypes.c_void_p(idxs[i].data_ptr()),
-                               wsp[w][0], wsp[w][1], sp)
-
-    def recheck(i, w=0, on_side=False):
-        return L.vdf_fp64_recheck(ctypes.c_void_p(ins[i].data_ptr()), M, N, WIN, 1, P, 0, Q,
-                                  ctypes.c_void_p(outs[i].data_ptr()), ctypes.c_void_p(idxs[i].data_ptr()),
-                                  wsp[w][0], wsp[w][1], sp2 if on_side else sp)
-
-    def fp64_step(i):
-        return L.vdf_filter(ctypes.c_void_p(ins[i].data_ptr()), M, N, WIN, 1, P, 0, Q, 0,
-                            ctypes.c_void_p(outs[i].data_ptr()), ctypes.c_void_p(idxs[i].data_ptr()), None, None,
-                            0, sp)
-
-    def check(rc):
-        if rc != 0:
-            raise RuntimeError(f"libvdf: {L.vdf_strerror(rc).decode()} {L.vdf_last_cuda_error().decode()}")
-
-    def barrier():
-        if ws > 1:
-            dist.barrier()
-        torch.cuda.synchronize(dev)
-
-    def max_over_ranks(v: float) -> float:
-        return reduce_max(v, ws, dev)
-
-    # ---- FP32 certified path (the headline) --------------------------------
-    # the library's autotuner picks the tile shape for this configuration
-    if args.shape is None:
-        shape, tune_ms = vdf.autotune(ins[0], WIN, FILTER, P, DIST, Q, reps=5)
-    else:
-        shape = args.shape
-        vdf.set_tuned_shape(WIN, FILTER, DIST, shape)
-    tw, th = vdf.tile_shapes()[shape]
-    for s in range(args.warmup):
-        check(fp32_pass(s % FRAMES))
-        check(recheck(s % FRAMES))
     K = args.steps
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
-           torch.cuda.Event(enable_timing=True)) for _ in range(K)]
-    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    rechecked = []
-    barrier()
-    with ClockSampler(local) as clk:
-        t_wall = time.perf_counter()
-        t_start.record(stream)
-        for s in range(K):
-            i, w = s % FRAMES, s % 3
-            if s >= 3:
-                stream.wait_event(ev[s - 3][2])    # workspace w is free again
-            ev[s][0].record(stream)
-            check(fp32_pass(i, w))
-            ev[s][1].record(stream)
-            side.wait_event(ev[s][1])
-            check(recheck(i, w, on_side=True))
-            ev[s][2].record(side)
-        stream.wait_event(ev[K - 1][2])
-        t_end.record(stream)
-        barrier()
-        t_wall = time.perf_counter() - t_wall
-    kernel_ms = [a.elapsed_time(b) for a, b, _ in ev]
-    step_ms = [a.elapsed_time(c) for a, _, c in ev]
-    total_ms = max_over_ranks(t_start.elapsed_time(t_end))
-    clocks = clk.summary()
-    for i in range(min(FRAMES, K)):   # recheck counts per frame (untimed)
-        check(fp32_pass(i))
-        torch.cuda.synchronize(dev)
-        rechecked.append(vdf.workspace_stats(wst[0])[0])
-    value = whole_job_rate(K * M * N, ws, total_ms)
-
-    # ---- plain FP64 GPU path (the metric's denominator) ---------------------
     K64 = args.fp64_steps or max(3, min(K, 10))
-    for s in range(3):
-        check(fp64_step(s % FRAMES))
-    barrier()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for s in range(K64):
-        check(fp64_step(s % FRAMES))
-    e1.record(stream)
-    barrier()
-    fp64_ms = max_over_ranks(e0.elapsed_time(e1)) / K64
-    fp64_value = whole_job_rate(M * N, ws, fp64_ms)
 
-    # ---- end to end through the host-buffer C ABI ---------------------------
-    # vdf_filter_host_frames: Ke frames from pinned host memory to pinned host
-    # memory in one call; every frame's upload and download is inside the
-    # timed region, overlapped with the filtering of its neighbours
-    pin_in = [torch.from_numpy(f).pin_memory() for f in host_frames[:4]]
-    pin_out = [torch.empty((M, N, 3), dtype=torch.uint8).pin_memory() for _ in range(2)]
-    pin_idx = [torch.empty((M, N), dtype=torch.int8).pin_memory() for _ in range(2)]
-    dbuf = torch.empty(vdf.host_frames_buffer_bytes(M, N, "fp32") + 256, dtype=torch.uint8, device=dev)
-    bp, bl = vdf._aligned(dbuf)
-    Ke = max(3, min(K, 100))
-    VP = ctypes.c_void_p
-
-    def e2e_call(count):
-        ins = (VP * count)(*[pin_in[s % 4].data_ptr() for s in range(count)])
-        outs = (VP * count)(*[pin_out[s % 2].data_ptr() for s in range(count)])
-        idxs = (VP * count)(*[pin_idx[s % 2].data_ptr() for s in range(count)])
-        return L.vdf_filter_host_frames(ins, outs, idxs, count, M, N, WIN, 1, P, 0, Q, 1, bp, bl, sp)
-    check(e2e_call(3))
-    barrier()
-    t0 = time.perf_counter()
-    check(e2e_call(Ke))
-    barrier()
-    e2e_s = max_over_ranks(time.perf_counter() - t0)
-    e2e_value = whole_job_rate(Ke * M * N, ws, e2e_s * 1e3)
+    # clocks are sampled every 20 ms over the FP32 timed region, the FP64 leg
+    # and the end-to-end leg (the FP32 region alone is a few milliseconds)
+    Mh, Nh, metric, config = M, N, METRIC, dict(CONFIG)
+    with ClockSampler(local) as clk:
+        r = measure_frames(L, vdf, torch, dev, sp, stream, M, N, NOISE, FRAMES, frame_seed(rank), K, args.warmup,
+                           args.shape, K64, ws, e2e_frames=max(3, min(K, 100)))
+    clocks = clk.summary()
+    clocks["span"] = "FP32 timed region + FP64 leg + end-to-end leg"
+    value = whole_job_rate(K * Mh * Nh, ws, r["total_ms"])
+    fp64_value = whole_job_rate(Mh * Nh, ws, r["fp64_ms"])
+    e2e_value = whole_job_rate(r["e2e_frames"] * Mh * Nh, ws, r["e2e_s"] * 1e3)
 
     # ---- roofline of the dominant kernel (FP32 tile kernel) -----------------
-    k_ms = statistics.mean(kernel_ms)
-    achieved = ALU_OPS_PER_PIXEL * M * N / (k_ms * 1e-3) / 1e12
+    ops = opcount(WIN, FILTER, DIST)
+    k_ms = r["kernel_ms"]
+    achieved = ops * Mh * Nh / (k_ms * 1e-3) / 1e12
     peak = SMS * FP32_LANES_PER_SM * 2.070e9 / 1e12
+    tw, th = r["shape"]
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "T FP32-pipe ops/s",
                 "frac": achieved / peak, "traffic": TRAFFIC_BY_SOURCE.get(kernel_source_hash()),
                 "kernel": f"vdf::tile_kernel<R=2,DDF,EXACT,FP32> {tw}x{th} tile (autotuned)", "kernel_ms": k_ms,
-                "ops_per_pixel": ALU_OPS_PER_PIXEL,
-                "peak_basis": "152 SMs x 128 FP32 lanes x 2070 MHz max SM clock",
-                "hbm_gbs_achieved": 7.0 * M * N / (k_ms * 1e-3) / 1e9,
+                "ops_per_pixel": ops,
+                "ops_basis": "opcount(5, 'ddf', 'exact'): 40 pair terms x (25 angle + 7 L2) + 600 aggregation "
+                             "adds + 24 compares + 50 logs, fixed before tuning",
+                "peak_basis": "nominal: 152 SMs x 128 FP32 lanes x 2070 MHz max SM clock",
+                "sm_mhz_sampled": clocks.get("sm_mhz"),
+                "hbm_gbs_achieved": 7.0 * Mh * Nh / (k_ms * 1e-3) / 1e9,
                 "hbm_gbs_peak_measured": measured_peaks().get("hbm_gbs")}
+
+    extras = {}
+    saved = (M, N, NOISE, FRAMES, WORKLOAD, METRIC, CONFIG)
+    if ws == 1 and not args.no_extras:
+        Ke = max(3, min(K, 20))
+        use_4k_workload()
+        with ClockSampler(local) as clk4:
+            r4 = measure_frames(L, vdf, torch, dev, sp, stream, M, N, NOISE, FRAMES, 100, Ke, args.warmup, args.shape,
+                                max(3, min(Ke, 4)), ws)
+        extras["ddf5_4k"] = {
+            "workload": WORKLOAD, "value": Ke * M * N / (r4["total_ms"] * 1e-3) / 1e6, "unit": UNIT,
+            "ms_per_step": r4["total_ms"] / Ke, "steps": Ke, "kernel_ms": r4["kernel_ms"],
+            "fp64_value": M * N / (r4["fp64_ms"] * 1e-3) / 1e6, "speedup_vs_fp64": r4["fp64_ms"] * Ke / r4["total_ms"],
+            "recheck_fraction": r4["recheck_fraction"], "structural_tie_fraction": r4["structural_tie_fraction"],
+            "mismatches_vs_fp64": r4["mismatches_vs_fp64"], "frames_compared": r4["frames_compared"],
+            "roofline_frac": opcount(WIN, FILTER, DIST) * M * N / (r4["kernel_ms"] * 1e-3) / 1e12 / peak,
+            "clocks": clk4.summary()}
+        ba = argparse.Namespace(steps=Ke, warmup=args.warmup)
+        b = run_batch_workload(ba, emit=False)
+        extras["batch"] = {k: b[k] for k in ("metric", "value", "unit", "ms_per_step", "steps", "recheck_fraction",
+                                             "structural_tie_fraction", "gpu_launches", "clocks")}
+        extras["batch"]["roofline_frac"] = b["roofline"]["frac"]
+        extras["batch"]["persistent_form_value"] = b["persistent_form"]["value"]
+        a = run_autograd_workload(ba, emit=False)
+        extras["autograd"] = {k: a[k] for k in ("metric", "value", "unit", "ms_per_step", "steps", "forward_ms",
+                                                "backward_ms", "forward_fp64_ms", "forward_recheck_fraction",
+                                                "gpu_launches", "clocks")}
+        extras["autograd"]["backward_roofline"] = a["roofline"]
+    set_workload(*saved)
 
     if rank != 0:
         if ws > 1:
@@ -720,21 +833,26 @@ def main():
     cpu = None
     if not args.no_cpu_baseline and ws == 1:
         cpu = cpu_oracle_rate()
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": args.warmup,
-            "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32+f64", "data": "synthetic", "config": CONFIG,
-            "fp64_path": {"value": fp64_value, "unit": UNIT, "ms_per_step": fp64_ms, "steps": K64},
+    line = {"metric": metric, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": args.warmup,
+            "ms_per_step": r["total_ms"] / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64", "data": "synthetic", "config": config,
+            "fp64_path": {"value": fp64_value, "unit": UNIT, "ms_per_step": r["fp64_ms"], "steps": K64},
             "speedup_vs_fp64": value / fp64_value,
-            "recheck_fraction": float(np.mean(rechecked)) / (M * N) if rechecked else None,
-            "step_ms_mean": statistics.mean(step_ms), "wall_s": t_wall,
+            "mismatches_vs_fp64": r["mismatches_vs_fp64"],
+            "mismatch_check": f"member index and RGB of every pixel of {r['frames_compared']} frames, FP32 path "
+                              "(with its recheck) against the plain FP64 path",
+            "recheck_fraction": r["recheck_fraction"], "structural_tie_fraction": r["structural_tie_fraction"],
+            "step_ms_mean": r["step_ms_mean"], "wall_s": r["wall_s"],
             "pipelining": "FP64 recheck of frame i on a second stream overlaps the FP32 passes of frames "
                           "i+1 and i+2 (three workspaces)",
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 3 * M * N,
-                    "d2h_bytes_per_step": 4 * M * N, "steps": Ke,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 3 * Mh * Nh,
+                    "d2h_bytes_per_step": 4 * Mh * Nh, "steps": r["e2e_frames"],
                     "api": "vdf_filter_host_frames (pinned host frames in and out; uploads and downloads "
                            "overlapped with the filtering of neighbouring frames)"},
             "gpu_launches": 2 * K,
             "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks}
+    if extras:
+        line["extra"] = extras
     print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()

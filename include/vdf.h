@@ -96,7 +96,13 @@ size_t vdf_workspace_bytes(int M, int N, int precision);
  *              per pixel and member i, sum_j A_ij then sum_j L2_ij (the
  *              latter 0 for BVDF).  For Method 2 in DDF the first value is
  *              1.436437 * sum_j B_ij + 0.027664 * n (Eq. (10)).
- *   win        3 or 5.   filter: vdf_filter_kind (VDF_VMF at order 2).
+ *   win        3, 5 or 7 (Section II's sqrt(n) x sqrt(n) window; n = 49
+ *              still fits the int8 index).  3 and 5 run the tile kernels,
+ *              which compute each pair term once for all windows sharing
+ *              it; 7 runs a kernel with one warp per output pixel (every
+ *              member's aggregate formed over its window directly; in FP64
+ *              each unordered pair once per window).
+ *              filter: vdf_filter_kind (VDF_VMF at order 2).
  *              p: DDF exponent, [0, 1].
  *   dist_mode  vdf_dist_mode (ignored for VDF_VMF).  minimax_q: 2, 3 or 4
  *              (used for MINIMAX only).
@@ -134,6 +140,7 @@ int vdf_filter_lp(const uint8_t *img, int M, int N, int win, int filter, double 
  * w_j = 1 otherwise.  Readings: Eq. (9) names the outputs of the test CWDDF^k
  * but defines CWVMF^k, which are used; the test is strict.  The paper sets
  * lambda = 2 and T = 10.8.
+ *   win        3 or 5 (VDF_E_UNSUPPORTED for 7).
  *   lambda     1 .. d - 2 with d = (win*win + 1)/2 (so every level k <= d).
  *   T          finite threshold.
  * Other arguments as vdf_filter (filter fixed to the DDF, p = 1/2).  With
@@ -235,7 +242,7 @@ int vdf_filter_host_frames(const uint8_t *const *img_host, uint8_t *const *out_h
  * float32 (NCHW, any non-negative values, e.g. RGB in [0, 1]); out: same
  * shape; index_out: device, B x M x N int8 (may be NULL, but the backward
  * pass needs it).  Only VDF_BVDF and VDF_DDF with VDF_DIST_EXACT are
- * supported for float input (else VDF_E_UNSUPPORTED).  The
+ * supported for float input, at windows 3 and 5 (else VDF_E_UNSUPPORTED).  The
  * FP64 precision computes the pair terms from the float32 values exactly
  * promoted to double.  VDF_PREC_FP32_RECHECK computes them in FP32 on
  * exponent-normalised pixels with certified bounds (Kahan cross products)
@@ -262,6 +269,7 @@ int vdf_filter_f32(const float *img, int B, int M, int N, int win, int filter, d
  * There is no counterpart in the paper (it does not differentiate the
  * filters); this is the exact gradient of the selection away from ties.
  */
+/* win: 3 or 5. */
 int vdf_backward_f32(const float *grad_y, const int8_t *index, int B, int M, int N, int win, float *grad_x,
                      void *stream);
 
@@ -296,6 +304,7 @@ int vdf_filter_noalloc(const uint8_t *img, int M, int N, int win, int filter, do
  * configuration (`reps` timed launches each after one warm-up, CUDA events
  * on `stream`; the call waits for the stream), records the fastest for
  * (win, filter, dist_mode) in a process-wide table used by vdf_filter,
+ * (windows 3 and 5: the 7x7 kernel has no tile shapes, VDF_E_UNSUPPORTED)
  * vdf_fp32_pass and vdf_plan_create, and returns it in *best_shape and its
  * mean time in *best_ms.  Buffers and workspace as for vdf_fp32_pass (the
  * image is filtered; out / index_out receive valid results).
@@ -369,7 +378,8 @@ void vdf_plan_destroy(vdf_plan *plan);
  * bounds, without selection.  fe_out: device, M*N*n*2 floats: f then E per
  * member.  BVDF: f is the aggregate.  DDF: f = (sum A)^(4p) (sum L2)^(4-4p)
  * (= Omega^4) when 4p is an integer, else f = p log2 sum A + (1-p) log2
- * sum L2.  The true value of f lies in [f - E, f + E].
+ * sum L2.  The true value of f lies in [f - E, f + E].  Windows 3 and 5
+ * (VDF_E_UNSUPPORTED for 7).
  */
 int vdf_debug_fp32_scores(const uint8_t *img, int M, int N, int win, int filter, double p, int dist_mode,
                           int minimax_q, float *fe_out, void *stream);

@@ -27,6 +27,7 @@ UNIT_FLAGS = {
     "vdf_fp64.cu": ["-fmad=false"],
     "vdf_fp64_lp.cu": ["-fmad=false"],
     "vdf_acw64.cu": ["-fmad=false"],
+    "vdf_win7_64.cu": ["-fmad=false"],
     # FP32 tile kernels: no denormal can occur (integer-valued data; every
     # guarded quantity is 0 or >= 1e-30), so flush-to-zero drops the denormal
     # fix-ups around rsqrtf/__log2f
@@ -39,6 +40,7 @@ UNIT_FLAGS = {
     "vdf_fp32f.cu": ["-ftz=true"],
     "vdf_fp32_lp.cu": ["-ftz=true"],
     "vdf_acw32.cu": ["-ftz=true"],
+    "vdf_win7_32.cu": ["-ftz=true"],
 }
 
 

@@ -9,6 +9,7 @@
 
 #include "../../include/vdf.h"
 #include "vdf_dispatch.h"
+#include "vdf_win7.cuh"
 
 namespace {
 
@@ -30,7 +31,7 @@ constexpr size_t kCtrBytes = vdf::kCounterBlockBytes;
 bool valid_common(int M, int N, int win, int filter, double p, int dist, int q, int prec)
 {
     if (M < 1 || N < 1 || (long long)M * N > (1LL << 31) - 1) return false;
-    if (win != 3 && win != 5) return false;
+    if (win != 3 && win != 5 && win != 7) return false;
     if (filter != VDF_BVDF && filter != VDF_DDF && filter != VDF_VMF) return false;
     if (filter == VDF_DDF && !(p >= 0.0 && p <= 1.0)) return false;
     if (dist < VDF_DIST_EXACT || dist > VDF_DIST_RGB) return false;
@@ -70,6 +71,7 @@ int g_tuned[2][3][3] = {};
 
 int tuned_shape(int win, int filter, int dist)
 {
+    if (win != 3 && win != 5) return 0;   // the 7x7 window has no tile shapes
     std::lock_guard<std::mutex> lock(g_tune_mutex);
     return g_tuned[win / 2 - 1][filter][dist];
 }
@@ -183,7 +185,22 @@ static int fp32_pass_shape(const uint8_t *img, int M, int N, int win, int filter
     cudaStream_t st = (cudaStream_t)stream;
     const vdf::TileParams prm = tile_params(img, M, N, p, minimax_q, out, index_out, nullptr, workspace);
     cudaError_t e = cudaMemsetAsync(prm.recheck_ctr, 0, vdf::kCounterBlockBytes, st);
-    if (e == cudaSuccess) e = run_tile32(prm, win / 2, filter, dist_mode, norm, shape, st);
+    if (e == cudaSuccess && win == 7) {
+        vdf::Win7Params wp{};
+        wp.img = img;
+        wp.out = out;
+        wp.idx = index_out;
+        wp.list = prm.recheck_list;
+        wp.ctr = prm.recheck_ctr;
+        wp.cap = prm.recheck_cap;
+        wp.M = M;
+        wp.N = N;
+        wp.p = p;
+        wp.q = minimax_q;
+        e = vdf::run_win7_fp32(wp, filter, dist_mode, norm, num_sms(), st);
+    } else if (e == cudaSuccess) {
+        e = run_tile32(prm, win / 2, filter, dist_mode, norm, shape, st);
+    }
     return cuda_fail(e);
 }
 
@@ -214,6 +231,8 @@ static int fp64_recheck_norm(const uint8_t *img, int M, int N, int win, int filt
     rp.N = N;
     rp.p = p;
     rp.q = minimax_q;
+    if (win == 7)
+        return cuda_fail(vdf::run_win7_recheck(rp, filter, dist_mode, norm, recheck_blocks(), (cudaStream_t)stream));
     return cuda_fail(run_recheck_any(rp, win / 2, filter, dist_mode, norm, recheck_blocks(), (cudaStream_t)stream));
 }
 
@@ -251,6 +270,17 @@ int vdf_filter_lp(const uint8_t *img, int M, int N, int win, int filter, double 
                                workspace, workspace_bytes);
     if (rc != VDF_OK) return rc;
     if (filter == VDF_DDF && norm != vdf::NL2 && dist_mode != VDF_DIST_EXACT) return VDF_E_UNSUPPORTED;
+    if (precision == VDF_PREC_FP64 && win == 7) {
+        vdf::RecheckParams rp{};
+        rp.img = img;
+        rp.out = out;
+        rp.idx = index_out;
+        rp.M = M;
+        rp.N = N;
+        rp.p = p;
+        rp.q = minimax_q;
+        return cuda_fail(vdf::run_win7_fp64(rp, agg_out, filter, dist_mode, norm, num_sms(), (cudaStream_t)stream));
+    }
     if (precision == VDF_PREC_FP64) {
         const vdf::TileParams prm = tile_params(img, M, N, p, minimax_q, out, index_out, agg_out, nullptr);
         return cuda_fail(run_tile64(prm, win / 2, filter, dist_mode, norm, (cudaStream_t)stream));
@@ -269,6 +299,7 @@ int vdf_filter_acwddf(const uint8_t *img, int M, int N, int win, int dist_mode, 
     int rc = check_filter_args(img, M, N, win, VDF_DDF, 0.5, dist_mode, minimax_q, precision, out, index_out,
                                nullptr, workspace, workspace_bytes);
     if (rc != VDF_OK) return rc;
+    if (win == 7) return VDF_E_UNSUPPORTED;
     const int d1 = (win * win + 1) / 2;   // 1-based centre index: levels lambda .. lambda+2 must stay <= d
     if (lambda < 1 || lambda > d1 - 2 || !std::isfinite(T)) return VDF_E_INVALID;
     cudaStream_t st = (cudaStream_t)stream;
@@ -375,7 +406,7 @@ int vdf_filter_f32(const float *img, int B, int M, int N, int win, int filter, d
     if ((long long)B * M * N > (1LL << 31) - 1) return VDF_E_INVALID;
     const size_t bytes = (size_t)B * M * N * 3 * sizeof(float);
     if (overlaps(img, bytes, out, bytes)) return VDF_E_INVALID;
-    if (dist_mode != VDF_DIST_EXACT || filter == VDF_VMF) return VDF_E_UNSUPPORTED;
+    if (dist_mode != VDF_DIST_EXACT || filter == VDF_VMF || win == 7) return VDF_E_UNSUPPORTED;
     if (index_out && (overlaps(index_out, (size_t)B * M * N, img, bytes) || overlaps(index_out, (size_t)B * M * N, out, bytes)))
         return VDF_E_INVALID;
     vdf::TileParams prm{};
@@ -459,6 +490,7 @@ int vdf_autotune(const uint8_t *img, int M, int N, int win, int filter, double p
     int rc = check_filter_args(img, M, N, win, filter, p, dist_mode, minimax_q, VDF_PREC_FP32_RECHECK, out,
                                index_out, nullptr, workspace, workspace_bytes);
     if (rc != VDF_OK) return rc;
+    if (win == 7) return VDF_E_UNSUPPORTED;   // one kernel, no tile shapes to choose from
     if (reps < 1) reps = 1;
     cudaStream_t st = (cudaStream_t)stream;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -509,6 +541,7 @@ int vdf_debug_fp32_scores(const uint8_t *img, int M, int N, int win, int filter,
     if (filter == VDF_VMF) dist_mode = VDF_DIST_EXACT;
     if (!img || !fe_out || !valid_common(M, N, win, filter, p, dist_mode, minimax_q, VDF_PREC_FP32_RECHECK))
         return VDF_E_INVALID;
+    if (win == 7) return VDF_E_UNSUPPORTED;
     vdf::TileParams prm{};
     prm.img = img;
     prm.dbg_fe = fe_out;

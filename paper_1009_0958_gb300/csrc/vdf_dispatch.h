@@ -40,6 +40,14 @@ cudaError_t run_fp32_acw(const TileParams &prm, int R, int dist, int shape, cuda
 cudaError_t run_fp64_acw(const TileParams &prm, int R, int dist, cudaStream_t st);
 cudaError_t run_recheck_acw(const RecheckParams &prm, int R, int dist, int blocks, cudaStream_t st);
 
+// The 7x7 window (vdf_win7.cuh): FP32 certified kernel, FP64 path (agg may
+// be null) and the FP64 recheck of the pixels the FP32 kernel lists.
+struct Win7Params;
+cudaError_t run_win7_fp32(const Win7Params &prm, int filter, int dist, int norm, int sms, cudaStream_t st);
+cudaError_t run_win7_fp64(const RecheckParams &prm, double *agg, int filter, int dist, int norm, int sms,
+                          cudaStream_t st);
+cudaError_t run_win7_recheck(const RecheckParams &prm, int filter, int dist, int norm, int blocks, cudaStream_t st);
+
 // The argument checks of vdf_filter's FP32 path, except those of the workspace.
 int check_args_no_workspace(const uint8_t *img, int M, int N, int win, int filter, double p, int dist_mode,
                             int minimax_q, const uint8_t *out, const int8_t *index_out);

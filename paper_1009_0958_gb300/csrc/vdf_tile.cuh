@@ -1282,17 +1282,41 @@ struct RecheckCfg {
     static constexpr size_t SMEM = PER_WARP * WARPS;
 };
 
+// Member mask of a window: 32 bits up to 5x5, 64 bits for 7x7.
+template <int NW>
+using MemberMask = typename std::conditional<(NW > 32), unsigned long long, unsigned>::type;
+
+template <int NW>
+__device__ __forceinline__ int mask_ffs(MemberMask<NW> m)
+{
+    if constexpr (NW > 32) return __ffsll((long long)m);
+    else return __ffs(m);
+}
+
+template <int NW>
+__device__ __forceinline__ int mask_popc(MemberMask<NW> m)
+{
+    if constexpr (NW > 32) return __popcll(m);
+    else return __popc(m);
+}
+
 // Recheck of one listed pixel by one warp.  `base` is the warp's shared
 // memory (RecheckCfg::PER_WARP bytes, 16-byte aligned).
 // F32IN: img and out are float32 B x 3 x M x N and lin = (b M + y) N + x.
+// With every member in the mask this is the whole FP64 computation of the
+// pixel (the FP64 path of the 7x7 window); agg, when given, receives the
+// members' aggregates as the FP64 tile kernel writes them.
 template <int R, int FILTER, int DIST, bool F32IN = false, int NORM = NL2, bool ACW = false>
-__device__ __forceinline__ void recheck_pixel(const void *img, int M, int N, int lin, unsigned mask, void *out,
-                                              int8_t *idx, double p, int q, unsigned char *base, int lane,
-                                              int lam = 0, double T = 0.0)
+__device__ __forceinline__ void recheck_pixel(const void *img, int M, int N, int lin,
+                                              MemberMask<(2 * R + 1) * (2 * R + 1)> mask, void *out, int8_t *idx,
+                                              double p, int q, unsigned char *base, int lane, int lam = 0,
+                                              double T = 0.0, double *agg = nullptr)
 {
     using C = RecheckCfg<R, FILTER, DIST>;
     using PixT = typename std::conditional<F32IN, float4, int4>::type;
     constexpr int W = C::W, NW = C::NW;
+    using MaskT = MemberMask<NW>;
+    static_assert(!ACW || NW <= 32, "ACWDDF: windows up to 5x5");
     PixT *px = reinterpret_cast<PixT *>(base);
     double *Ma = reinterpret_cast<double *>(base + sizeof(int4) * NW);
     double *Ml = Ma + NW * NW;
@@ -1319,8 +1343,8 @@ __device__ __forceinline__ void recheck_pixel(const void *img, int M, int N, int
     // computed once (in the row of the lower one) and stored in both rows:
     // the r-th lowest member's row holds every j except the r members below
     // it, NW - r work items.
-    constexpr unsigned ALL = (NW == 32) ? 0xffffffffu : ((1u << NW) - 1u);
-    const int cnt = __popc(mask);
+    constexpr MaskT ALL = (NW == 8 * (int)sizeof(MaskT)) ? ~MaskT(0) : ((MaskT(1) << NW) - 1);
+    const int cnt = mask_popc<NW>(mask);
     const int items = cnt * NW - cnt * (cnt - 1) / 2;
     for (int t = lane; t < items; t += 32) {
         int r = 0, start = 0;
@@ -1328,12 +1352,12 @@ __device__ __forceinline__ void recheck_pixel(const void *img, int M, int N, int
             start += NW - r;
             ++r;
         }
-        unsigned mm = mask;
+        MaskT mm = mask;
         for (int s = 0; s < r; ++s) mm &= mm - 1;   // drop the r lowest members
-        const int i = __ffs(mm) - 1;
-        unsigned row = ALL & ~(mask & ((1u << i) - 1u));
+        const int i = mask_ffs<NW>(mm) - 1;
+        MaskT row = ALL & ~(mask & ((MaskT(1) << i) - 1));
         for (int s = start; s < t; ++s) row &= row - 1;
-        const int j = __ffs(row) - 1;
+        const int j = mask_ffs<NW>(row) - 1;
         double a, l = 0.0;   // VMF: a holds the distance term
         if constexpr (F32IN) {
             a = aterm64f(px[i], px[j]);
@@ -1352,10 +1376,10 @@ __device__ __forceinline__ void recheck_pixel(const void *img, int M, int N, int
         }
     }
     __syncwarp();
-    if (lane < NW) {
+    for (int m = lane; m < NW; m += 32) {
         double f = INFINITY;
-        if ((mask >> lane) & 1u) {
-            const int ey = lane / W - R;   // window offset (ey, ex), ex = lane % W - R
+        if ((mask >> m) & 1u) {
+            const int ey = m / W - R;   // window offset (ey, ex), ex = m % W - R
             double sa = 0.0, sl = 0.0;
             // dy order 0, +1, -1, +2, -2, ... restricted to the window's rows
             for (int s = 0; s <= 4 * R; ++s) {
@@ -1363,20 +1387,25 @@ __device__ __forceinline__ void recheck_pixel(const void *img, int M, int N, int
                 if (dy < -R - ey || dy > R - ey) continue;
                 // the row sum covers the window's full row (dx = -R-ex .. R-ex)
                 const int row = (ey + dy + R) * W;
-                double ra = Ma[lane * NW + row], rl = 0.0;
-                if constexpr (FILTER == DDF) rl = Ml[lane * NW + row];
+                double ra = Ma[m * NW + row], rl = 0.0;
+                if constexpr (FILTER == DDF) rl = Ml[m * NW + row];
                 for (int c = 1; c < W; ++c) {
-                    ra += Ma[lane * NW + row + c];
-                    if constexpr (FILTER == DDF) rl += Ml[lane * NW + row + c];
+                    ra += Ma[m * NW + row + c];
+                    if constexpr (FILTER == DDF) rl += Ml[m * NW + row + c];
                 }
                 sa += ra;
                 sl += rl;
             }
             if constexpr (FILTER == DDF && DIST == RGB) sa = __fma_rn(kSlope64, sa, (double)NW * kOffset64);
+            if (agg) {   // sum_j A, sum_j L (VMF: 0, sum_j L)
+                double *ag = agg + ((size_t)lin * NW + m) * 2;
+                ag[0] = FILTER == VMF ? 0.0 : sa;
+                ag[1] = FILTER == VMF ? sa : sl;
+            }
             f = score64<FILTER>(sa, sl, p);
-            if constexpr (ACW) fs[NW + lane] = sl;   // the member's L2 aggregate
+            if constexpr (ACW) fs[NW + m] = sl;   // the member's L2 aggregate
         }
-        fs[lane] = f;
+        fs[m] = f;
     }
     __syncwarp();
     if (lane == 0) {
@@ -1413,8 +1442,11 @@ __global__ void __launch_bounds__(32 * kRecheckWarps) recheck_kernel(const Reche
     const int nwarps = gridDim.x * C::WARPS;
     for (unsigned it = blockIdx.x * C::WARPS + wid; it < count; it += nwarps) {
         const int2 ent = prm.list[it];
-        recheck_pixel<R, FILTER, DIST, F32IN, NORM, ACW>(prm.img, prm.M, prm.N, ent.x, (unsigned)ent.y, prm.out,
-                                                         prm.idx, prm.p, prm.q, base, lane, prm.lam, prm.T);
+        // 7x7 windows are listed with every member (the mask field holds -1)
+        MemberMask<C::NW> mask = (unsigned)ent.y;
+        if constexpr (C::NW > 32) mask = (MemberMask<C::NW>(1) << C::NW) - 1;
+        recheck_pixel<R, FILTER, DIST, F32IN, NORM, ACW>(prm.img, prm.M, prm.N, ent.x, mask, prm.out, prm.idx, prm.p,
+                                                         prm.q, base, lane, prm.lam, prm.T);
     }
 }
 

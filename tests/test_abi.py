@@ -66,7 +66,7 @@ def test_strerror_and_sizes(L):
 
 
 @pytest.mark.parametrize("args", [
-    dict(img=None), dict(M=0), dict(N=-1), dict(win=4), dict(win=7), dict(filter=3), dict(filter=-1),
+    dict(img=None), dict(M=0), dict(N=-1), dict(win=4), dict(win=9), dict(win=1), dict(filter=3), dict(filter=-1),
     dict(filter=1, p=1.5), dict(filter=1, p=-0.1),
     dict(dist=3), dict(dist=1, q=5), dict(precision=2),
 ])
@@ -106,6 +106,17 @@ def test_acwddf_arguments_checked_on_host(L, B):
     assert call(3, 2, float("inf")) == -1 and call(3, 2, float("nan")) == -1
     assert call(4, 2, 10.8) == -1 and call(3, 2, 10.8, dist=1, q=5) == -1
     assert call(3, 2, 10.8, precision=1) == -5    # valid, but no workspace
+    assert call(7, 2, 10.8) == -6                  # the 7x7 window is not offered for the ACWDDF
+
+
+def test_window_7_limits_on_host(L, B):
+    """The 7x7 window is accepted by the uint8 filters, not by the float path,
+    the backward pass, the autotuner or the tuned-shape table."""
+    img, out = B
+    assert L.vdf_filter(img, 8, 8, 7, 1, 0.25, 0, 4, 1, out, None, None, None, 0, None) == -5   # needs a workspace
+    assert L.vdf_filter_f32(img, 1, 8, 8, 7, 1, 0.25, 0, 4, 0, out, None, None, 0, None) == -6
+    assert L.vdf_backward_f32(img, img, 1, 8, 8, 7, out, None) == -1
+    assert L.vdf_set_tuned_shape(7, 1, 0, 0) == -1 and L.vdf_get_tuned_shape(7, 1, 0) == -1
 
 
 def test_aliasing_and_workspace_checks(L, B):
