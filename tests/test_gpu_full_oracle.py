@@ -116,3 +116,36 @@ def test_tile_shapes_methods_1_and_2(V, O, small_image, shape, win, filter, p, d
     V.set_tuned_shape(win, filter, dist, 0)
     assert_same(out, idx, ref, f"shape {shape}")
     assert st["overflow"] == 0
+
+
+def _edge_images():
+    from tests.test_gpu_parity import EDGES
+    return EDGES
+
+
+@pytest.mark.parametrize("shape", [1, 2, 3])
+@pytest.mark.parametrize("name", ["1x1", "1x57", "45x1", "2x2", "constant", "black", "checker", "collinear"])
+@pytest.mark.parametrize("win,filter,p,dist", [(5, "ddf", 0.25, "exact"), (5, "bvdf", 0.5, "rgb"),
+                                               (3, "ddf", 0.3, "minimax"), (5, "vmf", 0.5, "exact")])
+def test_edge_images_every_shape(V, O, shape, name, win, filter, p, dist):
+    """Edge images (single pixel, single row or column, constant, black,
+    checkerboard, collinear) through every FP32 tile shape, including the
+    persistent form with its staged copies."""
+    img = _edge_images()[name]
+    ref = O.filter_u8(img, win, filter, p, dist, 4)
+    d = "exact" if filter == "vmf" else dist
+    out, idx, st = gpu(V, img, win, filter, p, d, 4, "fp32", shape=shape)
+    V.set_tuned_shape(win, filter, d, 0)
+    assert_same(out, idx, ref, f"shape {shape}")
+
+
+@pytest.mark.parametrize("M,N", [(17, 29), (130, 61), (333, 250)])
+def test_persistent_form_ragged_sizes(V, O, M, N):
+    """Odd widths (row pitches that are not multiples of 4 bytes), several
+    tiles per CTA and ragged tails through the persistent 28x16 form."""
+    from paper_1009_0958_gb300 import synth
+    img = synth.make_image(M, N, 21, 0.2, rectangles=6)[1]
+    ref = O.filter_u8(img, 5, "ddf", 0.25, "exact", 4)
+    out, idx, st = gpu(V, img, 5, "ddf", 0.25, "exact", 4, "fp32", shape=3)
+    V.set_tuned_shape(5, "ddf", "exact", 0)
+    assert_same(out, idx, ref, "persistent form")
