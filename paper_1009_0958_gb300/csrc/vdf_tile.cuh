@@ -26,7 +26,6 @@
 // aggregate adds the row sums in the order dy = 0, +1, -1, +2, -2, ...
 #pragma once
 
-#include <algorithm>
 #include <atomic>
 #include <type_traits>
 #include <utility>
@@ -1268,175 +1267,9 @@ __global__ void __launch_bounds__(C::NT, C::MINB) tile_kernel(const TileParams p
     tile_body<C, C::NT>(prm, blockIdx.z, blockIdx.x * C::TW, blockIdx.y * C::TH, smem);
 }
 
-// ------------------------------------------ persistent FP32 tile kernel ----
-// The FP32 kernels of uint8 images whose CTA fills an SM (one CTA per SM)
-// run persistently: each CTA walks over the tiles t = blockIdx.x,
-// blockIdx.x + gridDim.x, ... and, while it computes tile t, copies the bytes
-// of its next tile from global memory into a staging buffer with cp.async.
-// The tile's pixels are then converted from shared memory, so no tile waits
-// for a global-memory round trip (the one-shot kernel spends 7-8% of a tile
-// there).  The image must be 4-byte aligned.
-
-// 4-byte global -> shared copy; bytes beyond src_bytes (1..4) are zero-filled
-// and not read.
-__device__ __forceinline__ void cp_async4(void *dst, const void *src, int src_bytes)
-{
-    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(src), "r"(src_bytes) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
-
-// Staging buffer: one row of words per row of C, covering the bytes of pixel
-// columns clamp(x0 - 3R) .. clamp(x0 + TW + 3R - 1) from the word that holds
-// the first of them (3 PXW bytes plus up to 3 of alignment, rounded up).
-template <class C>
-struct StageCfg {
-    static constexpr int WORDS = (3 * C::PXW + 3) / 4 + 2;
-    static constexpr size_t BYTES = sizeof(unsigned) * WORDS * C::CH;
-    static constexpr size_t SMEM = C::SMEM + BYTES;   // staging buffer after the tile's own shared memory
-};
-
-__device__ __forceinline__ int clampi(int v, int lo, int hi) { return min(max(v, lo), hi); }
-
-// Issues the copies of tile (x0, y0)'s bytes (all threads; one commit group).
-template <class C>
-__device__ __forceinline__ void stage_tile(const TileParams &prm, int x0, int y0, unsigned *raw)
-{
-    constexpr int R = C::R, WORDS = StageCfg<C>::WORDS;
-    const uint8_t *img = (const uint8_t *)prm.img;
-    const size_t pitch = 3 * (size_t)prm.N, total = pitch * prm.M;
-    const int cl = clampi(x0 - 3 * R, 0, prm.N - 1), ch = clampi(x0 + C::TW + 3 * R - 1, 0, prm.N - 1);
-    for (int e = threadIdx.x; e < C::CH * WORDS; e += blockDim.x) {
-        const int r = e / WORDS, w = e - r * WORDS;
-        const size_t row = (size_t)clampi(y0 - R + r, 0, prm.M - 1) * pitch;
-        const size_t wa = ((row + 3 * cl) >> 2) + w;   // absolute word index
-        if (4 * wa < row + 3 * (size_t)ch + 3) {
-            const int nb = (int)min((size_t)4, total - 4 * wa);   // >= 1: the word starts inside the image
-            cp_async4(raw + e, img + 4 * wa, nb);
-        }
-    }
-    cp_async_commit();
-}
-
-// Step 1 from the staging buffer: pixels, keys and auxiliaries of C plus the
-// column margins, edge-replicated (no barrier).
-template <class C>
-__device__ __forceinline__ void convert_tile(const TileParams &prm, int x0, int y0, const unsigned *raw,
-                                             unsigned char *smem)
-{
-    constexpr int R = C::R, PXW = C::PXW, WORDS = StageCfg<C>::WORDS;
-    float4 *pix = reinterpret_cast<float4 *>(smem);
-    Aux *aux = reinterpret_cast<Aux *>(smem + C::PIX_BYTES);
-    unsigned *keys = reinterpret_cast<unsigned *>(smem + C::PIX_BYTES + C::AUX_BYTES);
-    const unsigned char *rb = reinterpret_cast<const unsigned char *>(raw);
-    const size_t pitch = 3 * (size_t)prm.N;
-    const int cl = clampi(x0 - 3 * R, 0, prm.N - 1);
-    for (int i = threadIdx.x; i < C::CH * PXW; i += blockDim.x) {
-        const int r = i / PXW, c = i - r * PXW;
-        const size_t row = (size_t)clampi(y0 - R + r, 0, prm.M - 1) * pitch;
-        const int gx = clampi(x0 - 3 * R + c, 0, prm.N - 1);
-        const int off = (int)(row + 3 * (size_t)gx - (((row + 3 * cl) >> 2) << 2));
-        const unsigned char *q = rb + 4 * WORDS * r + off;
-        const int x = q[0], y = q[1], z = q[2];
-        const float4 v = make_float4((float)x, (float)y, (float)z, (float)(x * x + y * y + z * z));
-        pix[i] = v;
-        keys[i] = (unsigned)x | ((unsigned)y << 8) | ((unsigned)z << 16);
-        if constexpr (C::AUX) aux[i] = make_aux<C::DIST>(v);
-    }
-}
-
-// The selection of one tile of the persistent kernel, as a called function:
-// with the slice pipeline and the selection inlined into one tile loop, the
-// register allocator spills several hundred bytes (values of one part stay
-// live through the other); a called selection keeps them apart.
-template <class C>
-__device__ __noinline__ void tile_select_call(const TileParams &prm, int x0, int y0, unsigned char *smem)
-{
-    tile_select<C>(prm, 0, x0, y0, smem, false, threadIdx.x);
-}
-
-template <class C>
-__global__ void __launch_bounds__(C::NT, 1) tile_kernel_persistent(const TileParams prm, int tiles_x, int ntiles)
-{
-    static_assert(!C::FP64 && !C::F32IN, "FP32 path of uint8 images");
-    using PT = typename C::PlaneT;
-    extern __shared__ __align__(16) unsigned char smem[];
-    unsigned *raw = reinterpret_cast<unsigned *>(smem + C::SMEM);
-    {
-        const int t = blockIdx.x;   // the grid never exceeds the tile count
-        stage_tile<C>(prm, (t % tiles_x) * C::TW, (t / tiles_x) * C::TH, raw);
-        cp_async_wait_all();
-        __syncthreads();
-        convert_tile<C>(prm, (t % tiles_x) * C::TW, (t / tiles_x) * C::TH, raw, smem);
-        __syncthreads();
-    }
-    // The body is written out here rather than through tile_rest: with the
-    // helper in between, the register allocator spills a few hundred bytes in
-    // this loop (measured with ptxas), and none this way.
-#pragma unroll 1
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        const int x0 = (t % tiles_x) * C::TW, y0 = (t / tiles_x) * C::TH;
-        const int tn = t + gridDim.x;
-        // the staging buffer was converted before the last barrier: refill it
-        if (tn < ntiles) stage_tile<C>(prm, (tn % tiles_x) * C::TW, (tn / tiles_x) * C::TH, raw);
-        float4 *pix = reinterpret_cast<float4 *>(smem);
-        Aux *aux = reinterpret_cast<Aux *>(smem + C::PIX_BYTES);
-        PT *planes = reinterpret_cast<PT *>(smem + C::PIX_BYTES + C::AUX_BYTES + C::KEY_BYTES);
-        auto *hw = reinterpret_cast<typename C::HwT *>(smem + C::PIX_BYTES + C::AUX_BYTES + C::KEY_BYTES + C::HW_OFFSET);
-        const int tid = threadIdx.x, cy = tid / C::CW, cx = tid % C::CW;
-        float4 self_px{};
-        Aux self_aux{};
-        PT self_term{};
-        if (tid < C::NC) {
-            self_px = pix[cy * C::PXW + cx + 2 * C::R];
-            if constexpr (C::AUX) self_aux = aux[cy * C::PXW + cx + 2 * C::R];
-            self_term = pair_term<C>(self_px, self_px, self_aux, self_aux, prm.q);
-        }
-        all_slices32<C>(std::make_integer_sequence<int, 2 * C::R + 1>{}, prm, x0, y0, pix, aux, planes,
-                        planes + C::PBUF, hw, tid, cy, cx, self_px, self_aux, self_term, prm.q);
-        tile_select_call<C>(prm, x0, y0, smem);
-        if (tn >= ntiles) break;
-        cp_async_wait_all();
-        __syncthreads();   // the selection is done with the pixels, every copy has landed
-        convert_tile<C>(prm, (tn % tiles_x) * C::TW, (tn / tiles_x) * C::TH, raw, smem);
-        __syncthreads();
-    }
-}
-
-// The persistent form is used for FP32 kernels of uint8 images that run one
-// CTA per SM (two resident CTAs already overlap each other's load phase),
-// when the staging buffer still fits beside the tile's shared memory.
-// Only where ptxas keeps the tile loop free of spills: the 640-thread shape
-// (96 registers per thread) without the ACWDDF selection.
-template <class C>
-constexpr bool kPersistent = !C::FP64 && !C::F32IN && !C::ACW && C::MINB == 1 && C::NT == 640 &&
-                             StageCfg<C>::SMEM <= 227 * 1024;
-
 template <class C>
 cudaError_t launch_tile(const TileParams &prm, cudaStream_t st)
 {
-    if constexpr (kPersistent<C>) {
-        if (!prm.dbg_fe && prm.B == 1 && ((uintptr_t)prm.img & 3) == 0) {
-            static std::atomic<bool> configured_p[kMaxDevices];
-            static std::atomic<int> sms[kMaxDevices];
-            cudaError_t e = once_per_device(configured_p, [] {
-                return cudaFuncSetAttribute(tile_kernel_persistent<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            (int)StageCfg<C>::SMEM);
-            });
-            if (e != cudaSuccess) return e;
-            const int dev = current_device();
-            int n = sms[dev].load(std::memory_order_relaxed);
-            if (n <= 0) {
-                e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-                if (e != cudaSuccess) return e;
-                sms[dev].store(n, std::memory_order_relaxed);
-            }
-            const int tiles_x = (prm.N + C::TW - 1) / C::TW, ntiles = tiles_x * ((prm.M + C::TH - 1) / C::TH);
-            tile_kernel_persistent<C><<<std::min(ntiles, n), C::NT, StageCfg<C>::SMEM, st>>>(prm, tiles_x, ntiles);
-            return cudaGetLastError();
-        }
-    }
     // set once per instantiation and device
     static std::atomic<bool> configured[kMaxDevices];
     cudaError_t e = once_per_device(configured, [] {

@@ -129,8 +129,7 @@ def _edge_images():
                                                (3, "ddf", 0.3, "minimax"), (5, "vmf", 0.5, "exact")])
 def test_edge_images_every_shape(V, O, shape, name, win, filter, p, dist):
     """Edge images (single pixel, single row or column, constant, black,
-    checkerboard, collinear) through every FP32 tile shape, including the
-    persistent form with its staged copies."""
+    checkerboard, collinear) through every FP32 tile shape."""
     img = _edge_images()[name]
     ref = O.filter_u8(img, win, filter, p, dist, 4)
     d = "exact" if filter == "vmf" else dist
@@ -140,12 +139,12 @@ def test_edge_images_every_shape(V, O, shape, name, win, filter, p, dist):
 
 
 @pytest.mark.parametrize("M,N", [(17, 29), (130, 61), (333, 250)])
-def test_persistent_form_ragged_sizes(V, O, M, N):
-    """Odd widths (row pitches that are not multiples of 4 bytes), several
-    tiles per CTA and ragged tails through the persistent 28x16 form."""
+def test_28x16_shape_ragged_sizes(V, O, M, N):
+    """Odd widths (row pitches that are not multiples of 4 bytes) and ragged
+    tails through the 28x16 tile shape."""
     from paper_1009_0958_gb300 import synth
     img = synth.make_image(M, N, 21, 0.2, rectangles=6)[1]
     ref = O.filter_u8(img, 5, "ddf", 0.25, "exact", 4)
     out, idx, st = gpu(V, img, 5, "ddf", 0.25, "exact", 4, "fp32", shape=3)
     V.set_tuned_shape(5, "ddf", "exact", 0)
-    assert_same(out, idx, ref, "persistent form")
+    assert_same(out, idx, ref, "28x16 shape")
