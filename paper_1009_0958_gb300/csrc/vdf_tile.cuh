@@ -77,9 +77,10 @@ struct TileCfg {
     // DDF terms and aggregates are (angular, L2) pairs: .x and .y
     using Pair = typename std::conditional<FP64, double2, float2>::type;
     using PlaneT = typename std::conditional<FILTER == DDF, Pair, Real>::type;
-    // per (window, member) slot: the raw aggregates, later the score in place
-    using HwT = typename std::conditional<FP64, typename std::conditional<FILTER == DDF, double2, double>::type,
-                                          float2>::type;
+    // per (window, member) slot: the raw aggregates (FP64: later the score in
+    // place); one value for the single-aggregate filters (BVDF, VMF)
+    using HwT = typename std::conditional<FILTER == DDF, typename std::conditional<FP64, double2, float2>::type,
+                                          Real>::type;
     static constexpr size_t PIX_BYTES = sizeof(Pix) * CH * PXW;
     static constexpr size_t AUX_BYTES = AUX ? (sizeof(Aux) * CH * PXW + 15) / 16 * 16 : 0;
     // FP32: packed RGB key per pixel for the identical-vector test
@@ -102,8 +103,10 @@ struct TileCfg {
     static_assert(FP64 || PIX_BYTES >= sizeof(PlaneT) * (2 * R * CW + 2 * R), "FP32 plane reads stay in the block");
     // CTAs per SM the register budget is sized for: two when two fit in the
     // SM's 228 KB of shared memory (1 KB reserved per CTA) with at least 48
-    // registers per thread, so one CTA's barrier waits overlap the other's work
-    static constexpr int MINB = (2 * (SMEM + 1024) <= 228 * 1024 && 2 * NT * 48 <= 65536) ? 2 : 1;
+    // registers per thread (64 for 5x5, whose slice pipeline spills below
+    // that), so one CTA's barrier waits overlap the other's work
+    static constexpr int MINB =
+        (2 * (SMEM + 1024) <= 228 * 1024 && 2 * NT * (R == 1 ? 48 : 64) <= 65536) ? 2 : 1;
 };
 
 // ------------------------------------------------------------ scores ------
@@ -229,6 +232,13 @@ __device__ __forceinline__ float2 score32(float sa, float sl, float p, int quart
     E += 2.0f * kU * (fabsf(f) + lsum);                 // combine rounding, float p
     return make_float2(f, kSafety * E);
 }
+
+// Aggregates of an FP32 slot: (sum A, sum L2) for the DDF, one aggregate
+// otherwise (sum A for BVDF, sum L for the VMF).
+__device__ __forceinline__ float slot_a(const float2 &v) { return v.x; }
+__device__ __forceinline__ float slot_l(const float2 &v) { return v.y; }
+__device__ __forceinline__ float slot_a(float v) { return v; }
+__device__ __forceinline__ float slot_l(float) { return 0.0f; }
 
 // ---------------------------------------------------------- the kernel ----
 
@@ -608,8 +618,7 @@ __device__ __forceinline__ void all_slices32(std::integer_sequence<int, D...>, c
     auto emit = [&](int ey, int ex, const PT &a) {
         if (valid & (1u << ((ey + R) * W + (ex + R)))) {
             const int slot = ((cy - ey - R) * C::TW + (cx - ex - R)) * C::NW + (ey + R) * C::W + (ex + R);
-            if constexpr (C::FILTER == DDF) hw[slot] = a;
-            else hw[slot] = make_float2(a, 0.0f);
+            hw[slot] = a;
         }
     };
     PT st[2 * R][C::W];
@@ -654,10 +663,10 @@ __device__ __forceinline__ void score_slots(const TileParams &prm, int b, int x0
             if constexpr (C::FILTER == DDF) hw[s].x = sc;
             else hw[s] = sc;
         } else {
-            float sa = hw[s].x;
+            // (diagnostic only: the scores go to dbg_fe, no selection follows)
+            float sa = slot_a(hw[s]);
             if constexpr (C::FILTER == DDF && C::DIST == RGB) sa = fmaf(kSlope32, sa, (float)NW * kOffset32);
-            const float2 v = score32<R, C::FILTER, C::DIST, false, C::NORM>(sa, hw[s].y, (float)prm.p, quarter);
-            hw[s] = v;
+            const float2 v = score32<R, C::FILTER, C::DIST, false, C::NORM>(sa, slot_l(hw[s]), (float)prm.p, quarter);
             if (prm.dbg_fe) reinterpret_cast<float2 *>(prm.dbg_fe)[lin * NW + k] = v;
         }
     }
@@ -966,7 +975,7 @@ __device__ __forceinline__ void select_and_store(const TileParams &prm, int b, i
         if constexpr (C::F32IN) {
             float am[NW];
 #pragma unroll
-            for (int k = 0; k < NW; ++k) am[k] = C::FILTER == DDF ? fminf(f[k].x, f[k].y) : f[k].x;
+            for (int k = 0; k < NW; ++k) am[k] = C::FILTER == DDF ? fminf(slot_a(f[k]), slot_l(f[k])) : slot_a(f[k]);
             unsure = unsafe_tile || tree_min<NW>(am) < 0x1p-23f;
         }
         // Relative bounds (BVDF with the exact or chromaticity terms, and DDF
@@ -978,12 +987,12 @@ __device__ __forceinline__ void select_and_store(const TileParams &prm, int b, i
             float erel;
             if constexpr (C::FILTER == VMF) {
 #pragma unroll
-                for (int k = 0; k < NW; ++k) g[k] = f[k].x;
+                for (int k = 0; k < NW; ++k) g[k] = slot_a(f[k]);
                 // order 2: the L2 aggregate's bound; orders 1, infinity: exact
                 erel = C::NORM == NL2 ? kSafety * (6.0f + 4.0f * R) * kU : 0.0f;
             } else if constexpr (C::FILTER == BVDF) {
 #pragma unroll
-                for (int k = 0; k < NW; ++k) g[k] = f[k].x;
+                for (int k = 0; k < NW; ++k) g[k] = slot_a(f[k]);
                 erel = kSafety * ((C::DIST == RGB ? 11.0f : (C::F32IN ? 24.0f : 16.0f)) + 4.0f * R) * kU;
             } else {
                 // the uniform switch keeps each unrolled loop branch-free
@@ -991,9 +1000,9 @@ __device__ __forceinline__ void select_and_store(const TileParams &prm, int b, i
                 auto fill = [&](auto a) {
 #pragma unroll
                     for (int k = 0; k < NW; ++k) {
-                        float sa = f[k].x;   // >= 0 in these modes (sums of non-negative terms)
+                        float sa = slot_a(f[k]);   // >= 0 in these modes (sums of non-negative terms)
                         if constexpr (C::DIST == RGB) sa = fmaf(kSlope32, sa, (float)NW * kOffset32);
-                        g[k] = pow4_product<decltype(a)::value>(sa, f[k].y);
+                        g[k] = pow4_product<decltype(a)::value>(sa, slot_l(f[k]));
                     }
                 };
                 switch (quarter) {
@@ -1043,9 +1052,9 @@ __device__ __forceinline__ void select_and_store(const TileParams &prm, int b, i
             float2 v[NW];
 #pragma unroll
             for (int k = 0; k < NW; ++k) {
-                float sa = f[k].x;
+                float sa = slot_a(f[k]);
                 if constexpr (C::FILTER == DDF && C::DIST == RGB) sa = fmaf(kSlope32, sa, (float)NW * kOffset32);
-                v[k] = score32<R, C::FILTER, C::DIST, C::F32IN, C::NORM>(sa, f[k].y, (float)prm.p, quarter);
+                v[k] = score32<R, C::FILTER, C::DIST, C::F32IN, C::NORM>(sa, slot_l(f[k]), (float)prm.p, quarter);
             }
             // U = min (f + E); the near set {f - E <= U} holds every true minimiser
             float hi[NW];
