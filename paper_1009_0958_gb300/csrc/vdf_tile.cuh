@@ -822,9 +822,48 @@ __device__ __forceinline__ int acw_select32(const TileParams &prm, const float4 
         unsure = true;
         return argmin();
     };
+    // near set of n non-negative scores g with relative bounds E_k = erel g_k:
+    // {g - E <= min (g + E)} = {g <= gmin (1 + erel) / (1 - erel)}, the
+    // threshold evaluated with five roundings and padded by 1 + 6u (as in
+    // select_and_store), so the computed set contains the near set
+    auto near_rel = [&](const float *g, float erel) -> unsigned {
+        const float thr = tree_min<NW>(g) * ((1.0f + erel) / (1.0f - erel)) * (1.0f + 6.0f * kU);
+        return bit_mask<NW>([&](int k) { return g[k] <= thr; });
+    };
+    auto argmin_of = [&](const float *g) {
+        int arg = 0;
+        float best = g[0];
+#pragma unroll
+        for (int k = 1; k < NW; ++k)
+            if (g[k] < best) {
+                best = g[k];
+                arg = k;
+            }
+        return arg;
+    };
     // 1. the DDF, Eq. (3) (p = 1/2: Omega^4 = SA^2 SL^2 with its bound)
     int sel_ddf;
-    {
+    if constexpr (DIST != MINIMAX) {
+        // exact and chromaticity terms: relative bounds (pow4_erel)
+        float g[NW];
+#pragma unroll
+        for (int k = 0; k < NW; ++k) {
+            float sa = f[k].x;
+            if constexpr (DIST == RGB) sa = fmaf(kSlope32, sa, (float)NW * kOffset32);
+            g[k] = pow4_product<2>(sa, f[k].y);
+        }
+        const unsigned near = near_rel(g, pow4_erel<R, DIST>(2));
+        bool zeros = true;   // all near scores exactly 0: exact ties
+#pragma unroll
+        for (int k = 0; k < NW; ++k)
+            if ((near >> k) & 1u) zeros = zeros && g[k] == 0.0f;
+        if (zeros && near) {
+            tied = tied || (near & (near - 1)) != 0;
+            sel_ddf = ((near >> CENTRE) & 1u) ? CENTRE : __ffs(near) - 1;
+        } else {
+            sel_ddf = resolve(near, [&]() { return argmin_of(g); });
+        }
+    } else {
         float2 v[NW];
         float hi[NW];
 #pragma unroll
@@ -843,8 +882,7 @@ __device__ __forceinline__ int acw_select32(const TileParams &prm, const float4 
         if (zeros && near) {
             tied = tied || (near & (near - 1)) != 0;
             sel_ddf = ((near >> CENTRE) & 1u) ? CENTRE : __ffs(near) - 1;
-        }
-        else
+        } else {
             sel_ddf = resolve(near, [&]() {
                 int arg = 0;
                 float best = v[0].x;
@@ -856,6 +894,7 @@ __device__ __forceinline__ int acw_select32(const TileParams &prm, const float4 
                     }
                 return arg;
             });
+        }
     }
     // 2. the centre-weighted VMF levels and the switching sum
     const float4 xd = pix[P(CENTRE)];
@@ -865,32 +904,22 @@ __device__ __forceinline__ int acw_select32(const TileParams &prm, const float4 
         const float4 xk = pix[P(k)];
         lc[k] = l2term32(xk, xd, fmaf(xk.z, xd.z, fmaf(xk.y, xd.y, xk.x * xd.x)));
     }
+    // Level k scores sc = S + c Lc, all parts >= 0: S (the L2 aggregate) has
+    // relative error <= kS u, c Lc <= 6u (the centre distance; c is exact),
+    // the FMA one rounding, so |error| <= (kS S + 6 c Lc + sc) u <=
+    // (kS + 2) u sc (kS >= 6, S + c Lc <= sc (1 + u)): a relative bound,
+    // doubled like every FP32 bound.
     constexpr float kS = 6.0f + 4.0f * R;   // relative bound of an L2 aggregate (units of u)
+    constexpr float kLevelRel = kSafety * (kS + 2.0f) * kU;
     float sum = 0.0f, Es = 0.0f;
 #pragma unroll 1
     for (int lev = 0; lev < 3; ++lev) {
         const float c = (float)(NW - 2 * (prm.lam + lev) + 1);
-        float sc[NW], hi[NW], lo[NW];
+        float sc[NW];
 #pragma unroll
-        for (int k = 0; k < NW; ++k) {
-            sc[k] = fmaf(c, lc[k], f[k].y);
-            const float e = kSafety * kU * (kS * f[k].y + 6.0f * c * lc[k] + sc[k]);
-            hi[k] = sc[k] + e;
-            lo[k] = sc[k] - e;
-        }
-        const float U = tree_min<NW>(hi);
-        const unsigned near = bit_mask<NW>([&](int k) { return lo[k] <= U; });
-        const int y = resolve(near, [&]() {
-            int arg = 0;
-            float best = sc[0];
-#pragma unroll
-            for (int k = 1; k < NW; ++k)
-                if (sc[k] < best) {
-                    best = sc[k];
-                    arg = k;
-                }
-            return arg;
-        });
+        for (int k = 0; k < NW; ++k) sc[k] = fmaf(c, lc[k], f[k].y);
+        const unsigned near = near_rel(sc, kLevelRel);
+        const int y = resolve(near, [&]() { return argmin_of(sc); });
         // A(y, x_d) L2(y, x_d): relative (exact, Eq. (10)) or absolute (Method 1) bounds
         const float4 xy = pix[P(y)];
         const PairInts r = pair_ints(xy, xd);
