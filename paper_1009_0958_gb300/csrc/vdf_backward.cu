@@ -22,11 +22,9 @@ namespace {
 // and a ring around it are first staged in shared memory (entries outside
 // the image get index -1).  Then every staged pixel p within R of the tile
 // computes its source q = src(p) and, when q lies in the tile, sets bit
-// (p - q + (R, R)) in q's source mask (a shared-memory OR).  Then each warp
-// gathers one row of the tile, lane l for columns l, l + 32, ...: it adds the
-// gradients of the set bits, lowest first, i.e. in raster order of p.  The
-// sums pass through shared memory, and each thread stores kQ adjacent
-// columns of one row.
+// (p - q + (R, R)) in q's source mask (a shared-memory OR).  Finally each
+// thread gathers for kQ pixels of one row: it adds the gradients of the set
+// bits, lowest first, i.e. in raster order of p.
 //
 // Staging: with VEC (N a multiple of 4, 16-byte aligned gradients) rows are
 // read as float4 / 32-bit words over columns bx - 4 .. bx + kTX + 3 (every
@@ -119,21 +117,18 @@ __global__ void __launch_bounds__(256) backward_gather(const float *__restrict__
             atomicOr(&qm[ty][tx], 1u << ((py - qy + R) * W + (px - qx + R)));
     }
     __syncthreads();
-    // gather: warp w takes tile row w, lane l the columns l, l + 32, l + 64,
-    // l + 96, so a warp's reads of the staged gradients fall on consecutive
-    // columns (no shared-memory bank conflicts for equal source offsets)
-    static_assert(kTY * 32 == 256 && kTX == 32 * kQ, "one warp per tile row");
-    const int gty = tid >> 5, lane = tid & 31;
+    const int ty = tid / (kTX / kQ), x0 = (tid % (kTX / kQ)) * kQ;   // tile coordinates
+    const int y = by + ty, X0 = bx + x0;
+    if (y >= M || X0 >= N) return;
     float acc[3][kQ];
 #pragma unroll
     for (int j = 0; j < kQ; ++j) {
-        const int x = lane + 32 * j;
-        unsigned mask = qm[gty][x];
+        unsigned mask = qm[ty][x0 + j];
         float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f;
         while (mask) {
             const int n = __ffs(mask) - 1;
             mask &= mask - 1;
-            const int r = gty + n / W, c = x + C0 + n % W - R;
+            const int r = ty + n / W, c = x0 + j + C0 + n % W - R;
             a0 += sg[0][r][c];
             a1 += sg[1][r][c];
             a2 += sg[2][r][c];
@@ -142,30 +137,17 @@ __global__ void __launch_bounds__(256) backward_gather(const float *__restrict__
         acc[1][j] = a1;
         acc[2][j] = a2;
     }
-    // the sums go through shared memory (the staged gradients' space) so that
-    // each thread stores four adjacent columns with one float4 per channel
-    __syncthreads();
-    float(*so)[kTY][kTX] = reinterpret_cast<float(*)[kTY][kTX]>(&sg[0][0][0]);
-    static_assert(sizeof(float) * 3 * kTY * kTX <= sizeof(sg), "staged sums fit");
-#pragma unroll
-    for (int c = 0; c < 3; ++c)
-#pragma unroll
-        for (int j = 0; j < kQ; ++j) so[c][gty][lane + 32 * j] = acc[c][j];
-    __syncthreads();
-    const int ty = tid / (kTX / kQ), x0 = (tid % (kTX / kQ)) * kQ;   // tile coordinates
-    const int y = by + ty, X0 = bx + x0;
-    if (y >= M || X0 >= N) return;
     float *o = gx + (size_t)b * 3 * plane + (size_t)y * N + X0;
     if (VEC && X0 + kQ <= N) {
 #pragma unroll
         for (int c = 0; c < 3; ++c)
-            *reinterpret_cast<float4 *>(o + c * plane) = *reinterpret_cast<const float4 *>(&so[c][ty][x0]);
+            *reinterpret_cast<float4 *>(o + c * plane) = make_float4(acc[c][0], acc[c][1], acc[c][2], acc[c][3]);
     } else {
 #pragma unroll
         for (int c = 0; c < 3; ++c)
 #pragma unroll
             for (int j = 0; j < kQ; ++j)
-                if (X0 + j < N) o[c * plane + j] = so[c][ty][x0 + j];
+                if (X0 + j < N) o[c * plane + j] = acc[c][j];
     }
 }
 
