@@ -114,13 +114,13 @@ SMS, FP32_LANES_PER_SM = 152, 128
 
 # DRAM bytes per launch of the FP32 tile kernel, from one ncu capture, keyed
 # by a hash of the kernel sources it was taken on (null once they change).
-TRAFFIC_BY_SOURCE = {"68d1641ecb2a01ef": 6296320}   # profiles/tile_kernel_fp32_ddf5_1080p.md
+TRAFFIC_BY_SOURCE = {"5091f452eb0b7d29": 6297088}   # profiles/tile_kernel_fp32_ddf5_1080p.md
 
 
 # DRAM bytes per launch of the backward gather on the differentiable workload
 # (profiles/backward_gather_autograd_32x512x512.md), keyed like the above by a
 # hash of vdf_backward.cu only.
-BACKWARD_TRAFFIC_BY_SOURCE = {}
+BACKWARD_TRAFFIC_BY_SOURCE = {"44b820dcd4629e61": 166681856}   # 109,069,824 read + 57,612,032 written
 
 
 def backward_source_hash() -> str:
