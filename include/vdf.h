@@ -320,8 +320,11 @@ int vdf_get_tuned_shape(int win, int filter, int dist_mode);
 int vdf_set_tuned_shape(int win, int filter, int dist_mode, int shape);
 
 /*
- * Batches of uneven images (FP32 certified path, VDF_DIST_EXACT).  Each image has its own size, window (3 or 5), filter and
- * DDF exponent.  A plan holds, on the host, one descriptor per image with
+ * Batches of uneven images (FP32 certified path).  Each image has its own
+ * size, window (3 or 5), filter and DDF exponent; the distance mode (exact,
+ * Method 1 with degree minimax_q, or Method 2) is one per plan
+ * (vdf_plan_create: VDF_E_INVALID for another mode or, with Method 1, a q
+ * outside 2..4).  A plan holds, on the host, one descriptor per image with
  * the tile shape the autotuner table gives its configuration, and the tile
  * and pixel offsets of the batch.
  *   vdf_plan_create      validates the descriptors (the plan keeps a copy;

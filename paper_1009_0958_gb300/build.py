@@ -36,6 +36,9 @@ UNIT_FLAGS = {
     "vdf_fp32_s2.cu": ["-ftz=true"],
     "vdf_fp32_s3.cu": ["-ftz=true"],
     "vdf_batch.cu": ["-ftz=true"],
+    "vdf_batch_d0.cu": ["-ftz=true"],
+    "vdf_batch_d1.cu": ["-ftz=true"],
+    "vdf_batch_d2.cu": ["-ftz=true"],
     "vdf_debug.cu": ["-ftz=true"],
     "vdf_fp32f.cu": ["-ftz=true"],
     "vdf_fp32_lp.cu": ["-ftz=true"],

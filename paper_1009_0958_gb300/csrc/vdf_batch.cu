@@ -28,199 +28,11 @@
 #include <vector>
 
 #include "../../include/vdf.h"
-#include "vdf_dispatch.h"
+#include "vdf_batch_kernels.cuh"
 
 namespace vdf {
 
 namespace {
-
-struct BatchDesc {
-    const uint8_t *img;
-    uint8_t *out;
-    int8_t *idx;
-    int M, N;
-    int tiles_x;
-    int tile_base;   // first work item of this image within its group
-    int pix_base;    // first batch pixel offset of this image (ascending over the descriptor array)
-    int cfg;         // ((win/2 - 1) * 2 + filter) * kNumShapes32 + shape
-    double p;
-};
-
-struct BatchParams {
-    const BatchDesc *desc;   // the group's descriptors (tile kernel) or all of them (recheck kernel)
-    int count;
-    int total_tiles;         // work items of the group
-    unsigned *ctr;           // [0] recheck count, [1] overflow
-    unsigned *next_item;     // the group's work counter (persistent form)
-    const int *item_image;   // the group's image of every work item (one-CTA-per-item form)
-    int2 *list;
-    unsigned cap;
-    int q;
-};
-
-template <int CFG>
-struct BCfg {
-    static constexpr int SHAPE = CFG % kNumShapes32;
-    static constexpr int FILTER = (CFG / kNumShapes32) % 2;
-    static constexpr int R = CFG / (2 * kNumShapes32) + 1;
-    using C = TileCfg<R, FILTER, EXACT, false, false, kShapes32[SHAPE].tw, kShapes32[SHAPE].th>;
-};
-constexpr int kNumCfgs = 2 * 2 * kNumShapes32;
-
-// The persistent tile kernel of one configuration.
-template <int CFG>
-__global__ void __launch_bounds__(BCfg<CFG>::C::NT, BCfg<CFG>::C::MINB) batch_kernel(const BatchParams bp)
-{
-    using C = typename BCfg<CFG>::C;
-    extern __shared__ __align__(16) unsigned char smem[];
-    // The CTA's current item and the next one (taken from the queue one item
-    // ahead, so the atomic's round trip overlaps the current tile), and the
-    // current image: its descriptor and the first item past it.  A CTA's
-    // items only increase, so the image index only moves forward; most items
-    // fall in the image of the one before and need no descriptor load.
-    __shared__ int s_item[2];
-    __shared__ int s_img, s_end;
-    __shared__ BatchDesc s_desc;
-    if (threadIdx.x == 0) {
-        s_item[0] = (int)atomicAdd(bp.next_item, 1u);
-        s_img = -1;
-        s_end = 0;
-    }
-    for (int it = 0;; it ^= 1) {
-        __syncthreads();   // s_item[it] is published; the previous item is done with shared memory
-        const int item = s_item[it];
-        if (item >= bp.total_tiles) break;
-        int next = 0;
-        if (threadIdx.x == 0) {
-            next = (int)atomicAdd(bp.next_item, 1u);
-            if (item >= s_end) {
-                int img = s_img, end = s_end;
-                while (item >= end) {
-                    ++img;
-                    end = img + 1 < bp.count ? bp.desc[img + 1].tile_base : bp.total_tiles;
-                }
-                s_img = img;
-                s_end = end;
-                s_desc = bp.desc[img];
-            }
-        }
-        __syncthreads();   // s_desc is current
-        TileParams prm{};
-        prm.img = s_desc.img;
-        prm.out = s_desc.out;
-        prm.idx = s_desc.idx;
-        prm.recheck_list = bp.list;
-        prm.recheck_ctr = bp.ctr;
-        prm.recheck_cap = bp.cap;
-        prm.pix_base = s_desc.pix_base;
-        prm.M = s_desc.M;
-        prm.N = s_desc.N;
-        prm.B = 1;
-        prm.p = s_desc.p;
-        prm.q = bp.q;
-        const int t = item - s_desc.tile_base, tiles_x = s_desc.tiles_x;
-        tile_body<C, C::NT>(prm, 0, (t % tiles_x) * C::TW, (t / tiles_x) * C::TH, smem);
-        if (threadIdx.x == 0) s_item[it ^ 1] = next;
-    }
-}
-
-// The same work as one CTA per item: the item's image comes from the
-// per-item table, the block scheduler is the queue.  Straight-line code gets
-// the register allocation of the single-image tile kernel, which a loop
-// around the tile body does not.
-template <int CFG>
-__global__ void __launch_bounds__(BCfg<CFG>::C::NT, BCfg<CFG>::C::MINB) batch_item_kernel(const BatchParams bp)
-{
-    using C = typename BCfg<CFG>::C;
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int item = blockIdx.x;
-    const BatchDesc &d = bp.desc[bp.item_image[item]];
-    TileParams prm{};
-    prm.img = d.img;
-    prm.out = d.out;
-    prm.idx = d.idx;
-    prm.recheck_list = bp.list;
-    prm.recheck_ctr = bp.ctr;
-    prm.recheck_cap = bp.cap;
-    prm.pix_base = d.pix_base;
-    prm.M = d.M;
-    prm.N = d.N;
-    prm.B = 1;
-    prm.p = d.p;
-    prm.q = bp.q;
-    const int t = item - d.tile_base, tiles_x = d.tiles_x;
-    tile_body<C, C::NT>(prm, 0, (t % tiles_x) * C::TW, (t / tiles_x) * C::TH, smem);
-}
-
-// Launch of one group's kernel: persistent (one CTA per SM per resident
-// CTA), or one CTA per item.
-template <int CFG>
-cudaError_t launch_group(const BatchParams &bp, int sms, cudaStream_t st, bool persistent)
-{
-    using C = typename BCfg<CFG>::C;
-    if (persistent) batch_kernel<CFG><<<sms * C::MINB, C::NT, C::SMEM, st>>>(bp);
-    else batch_item_kernel<CFG><<<bp.total_tiles, C::NT, C::SMEM, st>>>(bp);
-    return cudaGetLastError();
-}
-
-// The shared-memory opt-in of both forms, set once for every configuration
-// before any launch (outside graph capture).
-template <int CFG>
-cudaError_t configure_group()
-{
-    cudaError_t e = cudaFuncSetAttribute(batch_item_kernel<CFG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)BCfg<CFG>::C::SMEM);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(batch_kernel<CFG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)BCfg<CFG>::C::SMEM);
-    return e;
-}
-
-using GroupLaunch = cudaError_t (*)(const BatchParams &, int, cudaStream_t, bool);
-using GroupConfigure = cudaError_t (*)();
-template <int... I>
-constexpr std::array<GroupLaunch, sizeof...(I)> group_launchers(std::integer_sequence<int, I...>)
-{
-    return {&launch_group<I>...};
-}
-template <int... I>
-constexpr std::array<GroupConfigure, sizeof...(I)> group_configurers(std::integer_sequence<int, I...>)
-{
-    return {&configure_group<I>...};
-}
-constexpr auto kGroupLaunch = group_launchers(std::make_integer_sequence<int, kNumCfgs>{});
-constexpr auto kGroupConfigure = group_configurers(std::make_integer_sequence<int, kNumCfgs>{});
-
-// Per-warp shared memory of the largest recheck configuration.
-constexpr size_t kRecheckPerWarp = RecheckCfg<2, DDF, EXACT>::PER_WARP;
-
-__global__ void __launch_bounds__(32 * kRecheckWarps) batch_recheck_kernel(const BatchParams bp)
-{
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    unsigned char *base = smem + wid * kRecheckPerWarp;
-    const unsigned count = min(bp.ctr[0], bp.cap);
-    const int nwarps = gridDim.x * kRecheckWarps;
-    for (unsigned it = blockIdx.x * kRecheckWarps + wid; it < count; it += nwarps) {
-        const int2 ent = bp.list[it];
-        int lo = 0, hi = bp.count - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (bp.desc[mid].pix_base <= ent.x) lo = mid;
-            else hi = mid - 1;
-        }
-        const BatchDesc d = bp.desc[lo];
-        const int lin = ent.x - d.pix_base;
-        const int rf = d.cfg / kNumShapes32;   // (R - 1) * 2 + filter
-        const unsigned mask = (unsigned)ent.y;
-        switch (rf) {
-        case 0: recheck_pixel<1, BVDF, EXACT>(d.img, d.M, d.N, lin, mask, d.out, d.idx, d.p, bp.q, base, lane); break;
-        case 1: recheck_pixel<1, DDF, EXACT>(d.img, d.M, d.N, lin, mask, d.out, d.idx, d.p, bp.q, base, lane); break;
-        case 2: recheck_pixel<2, BVDF, EXACT>(d.img, d.M, d.N, lin, mask, d.out, d.idx, d.p, bp.q, base, lane); break;
-        default: recheck_pixel<2, DDF, EXACT>(d.img, d.M, d.N, lin, mask, d.out, d.idx, d.p, bp.q, base, lane); break;
-        }
-    }
-}
 
 // recheck count, overflow flag, one work counter per configuration
 constexpr size_t kCtrBytes = 256;
@@ -245,6 +57,7 @@ struct vdf_plan {
     int total_tiles = 0;
     long long total_pixels = 0;
     int q = 4;
+    int dist = 0;   // distance mode of every image of the plan
     int sms = 1;
     std::atomic<bool> persistent{false};   // tile kernels in the persistent work-queue form
     std::mutex mutex;
@@ -295,16 +108,39 @@ vdf::BatchParams plan_params(const vdf_plan *plan, void *ws, int g)
     return bp;
 }
 
-int set_attributes()
+// the shared-memory opt-in of the plan's distance mode, once per device
+int set_attributes(int dist)
 {
-    static std::atomic<bool> done[vdf::kMaxDevices];
-    const cudaError_t err = vdf::once_per_device(done, [] {
-        cudaError_t e = cudaFuncSetAttribute(vdf::batch_recheck_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)(vdf::kRecheckPerWarp * vdf::kRecheckWarps));
-        for (int c = 0; c < vdf::kNumCfgs && e == cudaSuccess; ++c) e = vdf::kGroupConfigure[c]();
-        return e;
-    });
+    static std::atomic<bool> done[3][vdf::kMaxDevices];
+    cudaError_t err = cudaErrorInvalidValue;
+    switch (dist) {
+    case vdf::EXACT: err = vdf::once_per_device(done[0], [] { return vdf::BatchOps<vdf::EXACT>::configure(); }); break;
+    case vdf::MINIMAX:
+        err = vdf::once_per_device(done[1], [] { return vdf::BatchOps<vdf::MINIMAX>::configure(); });
+        break;
+    case vdf::RGB: err = vdf::once_per_device(done[2], [] { return vdf::BatchOps<vdf::RGB>::configure(); }); break;
+    }
     return err == cudaSuccess ? VDF_OK : VDF_E_CUDA;
+}
+
+cudaError_t launch_group(int dist, int cfg, const vdf::BatchParams &bp, int sms, cudaStream_t st, bool persistent)
+{
+    switch (dist) {
+    case vdf::EXACT: return vdf::BatchOps<vdf::EXACT>::launch(cfg, bp, sms, st, persistent);
+    case vdf::MINIMAX: return vdf::BatchOps<vdf::MINIMAX>::launch(cfg, bp, sms, st, persistent);
+    case vdf::RGB: return vdf::BatchOps<vdf::RGB>::launch(cfg, bp, sms, st, persistent);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_recheck(int dist, const vdf::BatchParams &bp, int blocks, cudaStream_t st)
+{
+    switch (dist) {
+    case vdf::EXACT: return vdf::BatchOps<vdf::EXACT>::recheck(bp, blocks, st);
+    case vdf::MINIMAX: return vdf::BatchOps<vdf::MINIMAX>::recheck(bp, blocks, st);
+    case vdf::RGB: return vdf::BatchOps<vdf::RGB>::recheck(bp, blocks, st);
+    }
+    return cudaErrorInvalidValue;
 }
 
 bool ws_ok(const vdf_plan *plan, const void *ws, size_t bytes)
@@ -320,10 +156,12 @@ int vdf_plan_create(vdf_plan **plan, const vdf_image_desc *descs, int count, int
 {
     if (!plan || !descs || count < 1) return VDF_E_INVALID;
     *plan = nullptr;
-    if (dist_mode != VDF_DIST_EXACT) return VDF_E_UNSUPPORTED;
+    if (dist_mode < VDF_DIST_EXACT || dist_mode > VDF_DIST_RGB) return VDF_E_INVALID;
+    if (dist_mode == VDF_DIST_MINIMAX && (minimax_q < 2 || minimax_q > 4)) return VDF_E_INVALID;
     vdf_plan *pl = new (std::nothrow) vdf_plan;
     if (!pl) return VDF_E_INVALID;
     pl->q = minimax_q;
+    pl->dist = dist_mode;
     pl->sms = plan_num_sms();
     std::vector<vdf::BatchDesc> all;
     for (int i = 0; i < count; ++i) {
@@ -401,19 +239,16 @@ int vdf_filter_batch(vdf_plan *plan, void *workspace, size_t workspace_bytes, vo
 {
     if (!plan) return VDF_E_INVALID;
     if (!ws_ok(plan, workspace, workspace_bytes)) return VDF_E_WORKSPACE;
-    int rc = set_attributes();
+    int rc = set_attributes(plan->dist);
     if (rc != VDF_OK) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     const int sms = plan->sms;
     const int ngroups = (int)plan->groups.size();
     cudaError_t e = cudaMemsetAsync(workspace, 0, vdf::kCtrBytes, st);
     for (int g = 0; g < ngroups && e == cudaSuccess; ++g)
-        e = vdf::kGroupLaunch[plan->groups[g].cfg](plan_params(plan, workspace, g), sms, st, plan->persistent.load());
-    if (e == cudaSuccess) {
-        vdf::batch_recheck_kernel<<<sms * 16, 32 * vdf::kRecheckWarps, vdf::kRecheckPerWarp * vdf::kRecheckWarps, st>>>(
-            plan_params(plan, workspace, -1));
-        e = cudaGetLastError();
-    }
+        e = launch_group(plan->dist, plan->groups[g].cfg, plan_params(plan, workspace, g), sms, st,
+                         plan->persistent.load());
+    if (e == cudaSuccess) e = launch_recheck(plan->dist, plan_params(plan, workspace, -1), sms * 16, st);
     return e == cudaSuccess ? VDF_OK : VDF_E_CUDA;
 }
 
@@ -421,7 +256,7 @@ int vdf_plan_graph_launch(vdf_plan *plan, void *workspace, size_t workspace_byte
 {
     if (!plan) return VDF_E_INVALID;
     if (!ws_ok(plan, workspace, workspace_bytes)) return VDF_E_WORKSPACE;
-    int rc = set_attributes();
+    int rc = set_attributes(plan->dist);
     if (rc != VDF_OK) return rc;
     std::lock_guard<std::mutex> lock(plan->mutex);
     if (!plan->exec || plan->exec_ws != workspace) {

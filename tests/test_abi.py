@@ -192,7 +192,12 @@ def test_plan_host_logic(L):
         h = P()
         assert L.vdf_plan_create(ctypes.byref(h), ctypes.cast(descs(items), P), 1, 0, 4) == -1
     h = P()
-    assert L.vdf_plan_create(ctypes.byref(h), ctypes.cast(descs(dims[:1]), P), 1, 1, 4) == -6   # exact mode only
+    assert L.vdf_plan_create(ctypes.byref(h), ctypes.cast(descs(dims[:1]), P), 1, 1, 5) == -1   # Method 1 needs q in 2..4
+    assert L.vdf_plan_create(ctypes.byref(h), ctypes.cast(descs(dims[:1]), P), 1, 3, 4) == -1   # no such mode
+    for dist in (1, 2):                                                                            # Methods 1 and 2
+        h2 = P()
+        assert L.vdf_plan_create(ctypes.byref(h2), ctypes.cast(descs(dims[:1]), P), 1, dist, 4) == 0
+        L.vdf_plan_destroy(h2)
     assert L.vdf_plan_create(ctypes.byref(h), None, 1, 0, 4) == -1
     over = (vdf.ImageDesc * 1)()
     over[0] = vdf.ImageDesc(0x100000, 0x100010, 0, 8, 8, 3, 0, 0.5)   # out overlaps img

@@ -24,7 +24,8 @@ def reset_shapes(V):
     yield
     for win in (3, 5):
         for f in ("bvdf", "ddf"):
-            V.set_tuned_shape(win, f, "exact", 0)
+            for d in ("exact", "minimax", "rgb"):
+                V.set_tuned_shape(win, f, d, 0)
 
 
 def batch_items(seed, count, hi=300, extra=True):
@@ -41,9 +42,9 @@ def batch_items(seed, count, hi=300, extra=True):
     return items
 
 
-def check_against_single(V, plan, prec="fp32"):
+def check_against_single(V, plan, prec="fp32", dist="exact", q=4):
     for it in plan.items:
-        o, i = V.filter(it["img"], it["win"], it["filter"], it["p"], "exact", 4, precision=prec)
+        o, i = V.filter(it["img"], it["win"], it["filter"], it["p"], dist, q, precision=prec)
         assert torch.equal(o, it["out"]) and torch.equal(i, it["index"])
 
 
@@ -59,6 +60,28 @@ def test_batch_equals_single_image_calls(V, shapes, persistent):
     check_against_single(V, plan, "fp64")
     rechecked, overflow = plan.stats()
     assert overflow == 0 and rechecked > 0
+
+
+@pytest.mark.parametrize("persistent", [False, True])
+@pytest.mark.parametrize("dist,q", [("minimax", 4), ("minimax", 3), ("rgb", 4)])
+@pytest.mark.parametrize("shapes", [(0, 0, 0, 0), (1, 2, 3, 1)])
+def test_batch_methods_1_and_2(V, dist, q, shapes, persistent):
+    """The paper's two speed-up methods (Section 2.1, Table 1; Section 2.2,
+    Eq. (7)) through the batch: every image equals the single-image path in
+    both precisions and the oracle."""
+    import oracle
+    oracle.build()
+    for (win, f), s in zip([(3, "bvdf"), (3, "ddf"), (5, "bvdf"), (5, "ddf")], shapes):
+        V.set_tuned_shape(win, f, dist, s)
+    plan = V.Plan(batch_items(4, 16, hi=160), dist=dist, q=q, persistent=persistent)
+    plan.run()
+    torch.cuda.synchronize()
+    check_against_single(V, plan, "fp32", dist, q)
+    check_against_single(V, plan, "fp64", dist, q)
+    for it in plan.items[:8]:
+        ref = oracle.filter_u8(it["img"].cpu().numpy(), it["win"], it["filter"], it["p"], dist, q)
+        assert np.array_equal(it["index"].cpu().numpy(), ref["idx"])
+    assert plan.stats()[1] == 0
 
 
 @pytest.mark.parametrize("persistent", [False, True])
@@ -117,7 +140,7 @@ def test_plan_rejects_bad_descriptors(V):
     with pytest.raises(V.VdfError):
         V.Plan([dict(img=x, win=4)])
     with pytest.raises(V.VdfError):
-        V.Plan([dict(img=x, win=3)], dist="minimax")
+        V.Plan([dict(img=x, win=3)], dist="minimax", q=5)
     with pytest.raises(V.VdfError):
         V.Plan([dict(img=x, win=3, filter="ddf", p=2.0)])
 
