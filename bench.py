@@ -114,7 +114,7 @@ SMS, FP32_LANES_PER_SM = 152, 128
 
 # DRAM bytes per launch of the FP32 tile kernel, from one ncu capture, keyed
 # by a hash of the kernel sources it was taken on (null once they change).
-TRAFFIC_BY_SOURCE = {"5091f452eb0b7d29": 6297088}   # profiles/tile_kernel_fp32_ddf5_1080p.md
+TRAFFIC_BY_SOURCE = {"21b9d6bff2b55497": 6262272}   # profiles/tile_kernel_fp32_ddf5_1080p.md
 
 
 # DRAM bytes per launch of the backward gather on the differentiable workload
@@ -130,7 +130,7 @@ def backward_source_hash() -> str:
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for f in ("vdf_tile.cuh", "vdf_internal.cuh", "vdf_fp32.cu"):
+    for f in ("vdf_tile.cuh", "vdf_internal.cuh", "vdf_fp32.cu", "vdf_fp32_inst.cuh", "vdf_dispatch.h"):
         with open(os.path.join(ROOT, "paper_1009_0958_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -788,7 +788,8 @@ def main():
     tw, th = r["shape"]
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "T FP32-pipe ops/s",
                 "frac": achieved / peak, "traffic": TRAFFIC_BY_SOURCE.get(kernel_source_hash()),
-                "kernel": f"vdf::tile_kernel<R=2,DDF,EXACT,FP32> {tw}x{th} tile (autotuned)", "kernel_ms": k_ms,
+                "kernel": f"vdf::tile_kernel<R=2,DDF,EXACT,FP32,score slots> {tw}x{th} tile (autotuned)",
+                "kernel_ms": k_ms,
                 "ops_per_pixel": ops,
                 "ops_basis": "opcount(5, 'ddf', 'exact'): 40 pair terms x (25 angle + 7 L2) + 600 aggregation "
                              "adds + 24 compares + 50 logs, fixed before tuning",

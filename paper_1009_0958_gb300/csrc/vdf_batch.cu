@@ -184,6 +184,9 @@ int vdf_plan_create(vdf_plan **plan, const vdf_image_desc *descs, int count, int
         bd.N = d.N;
         bd.tiles_x = (d.N + vdf::kShapes32[shape].tw - 1) / vdf::kShapes32[shape].tw;
         bd.cfg = ((d.win / 2 - 1) * 2 + d.filter) * vdf::kNumShapes32 + shape;
+        // DDF 5x5 at p = 1/4 (exact or chromaticity terms): the score-slot kernels
+        if (d.win == 5 && d.filter == VDF_DDF && dist_mode != VDF_DIST_MINIMAX && 4.0f * (float)d.p == 1.0f)
+            bd.cfg = vdf::kScoreCfg0 + shape;
         bd.p = d.p;
         all.push_back(bd);
     }

@@ -19,7 +19,7 @@ struct BatchDesc {
     int tiles_x;
     int tile_base;   // first work item of this image within its group
     int pix_base;    // first batch pixel offset of this image (ascending over the descriptor array)
-    int cfg;         // ((win/2 - 1) * 2 + filter) * kNumShapes32 + shape
+    int cfg;         // ((win/2 - 1) * 2 + filter) * kNumShapes32 + shape; kScoreCfg0 + shape: DDF 5x5, p = 1/4
     double p;
 };
 
@@ -35,14 +35,30 @@ struct BatchParams {
     int q;
 };
 
+// Configurations: window x filter x tile shape, then DDF 5x5 at p = 1/4
+// with score slots (exact and chromaticity terms) in every shape.
+constexpr int kScoreCfg0 = 2 * 2 * kNumShapes32;
+constexpr int kNumCfgs = kScoreCfg0 + kNumShapes32;
+
+// The configuration a kernel is instantiated for: Method 1 has no score-slot
+// configurations (its plans never use them), so those entries reuse the raw
+// DDF 5x5 kernels.
+template <int DIST, int CFG>
+constexpr int canonical_cfg()
+{
+    return (CFG >= kScoreCfg0 && DIST == MINIMAX) ? CFG - kNumShapes32 : CFG;
+}
+
 template <int DIST, int CFG>
 struct BCfg {
     static constexpr int SHAPE = CFG % kNumShapes32;
-    static constexpr int FILTER = (CFG / kNumShapes32) % 2;
-    static constexpr int R = CFG / (2 * kNumShapes32) + 1;
-    using C = TileCfg<R, FILTER, DIST, false, false, kShapes32[SHAPE].tw, kShapes32[SHAPE].th>;
+    static constexpr bool SCORE = CFG >= kScoreCfg0;
+    static_assert(!SCORE || DIST != MINIMAX, "no score slots for Method 1");
+    static constexpr int FILTER = SCORE ? DDF : (CFG / kNumShapes32) % 2;
+    static constexpr int R = SCORE ? 2 : CFG / (2 * kNumShapes32) + 1;
+    using C = TileCfg<R, FILTER, DIST, false, false, kShapes32[SHAPE].tw, kShapes32[SHAPE].th, NL2, false,
+                      SCORE ? 1 : -1>;
 };
-constexpr int kNumCfgs = 2 * 2 * kNumShapes32;
 
 // The persistent tile kernel of one configuration.
 template <int DIST, int CFG>
@@ -158,12 +174,12 @@ using GroupConfigure = cudaError_t (*)();
 template <int DIST, int... I>
 constexpr std::array<GroupLaunch, sizeof...(I)> group_launchers(std::integer_sequence<int, I...>)
 {
-    return {&launch_group<DIST, I>...};
+    return {&launch_group<DIST, canonical_cfg<DIST, I>()>...};
 }
 template <int DIST, int... I>
 constexpr std::array<GroupConfigure, sizeof...(I)> group_configurers(std::integer_sequence<int, I...>)
 {
-    return {&configure_group<DIST, I>...};
+    return {&configure_group<DIST, canonical_cfg<DIST, I>()>...};
 }
 
 // Per-warp shared memory of the largest recheck configuration.
@@ -187,7 +203,7 @@ __global__ void __launch_bounds__(32 * kRecheckWarps) batch_recheck_kernel(const
         }
         const BatchDesc d = bp.desc[lo];
         const int lin = ent.x - d.pix_base;
-        const int rf = d.cfg / kNumShapes32;   // (R - 1) * 2 + filter
+        const int rf = d.cfg / kNumShapes32;   // (R - 1) * 2 + filter; 4: DDF 5x5 with score slots
         const unsigned mask = (unsigned)ent.y;
         switch (rf) {
         case 0: recheck_pixel<1, BVDF, DIST>(d.img, d.M, d.N, lin, mask, d.out, d.idx, d.p, bp.q, base, lane); break;

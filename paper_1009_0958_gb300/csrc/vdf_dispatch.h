@@ -16,8 +16,10 @@ struct TileShape {
 };
 constexpr int kNumShapes32 = 4;
 // 28x16 gives a 640-thread block (a multiple of 128), which leaves 96
-// registers per thread for DDF 5x5 instead of the 80 of 32x16's 736.
-inline constexpr TileShape kShapes32[kNumShapes32] = {{32, 16}, {32, 8}, {16, 16}, {28, 16}};
+// registers per thread for DDF 5x5 instead of the 80 of 32x16's 736.  24x12
+// (448 threads) fits two blocks per SM where the slots are single values
+// (BVDF, VMF, and the DDF's score slots at p = 1/4).
+inline constexpr TileShape kShapes32[kNumShapes32] = {{32, 16}, {32, 8}, {24, 12}, {28, 16}};
 cudaError_t run_fp32(const TileParams &prm, int R, int filter, int dist, int shape, cudaStream_t st);
 // Gradient gather of the float32 path.
 cudaError_t run_backward(const float *gy, const int8_t *idx, float *gx, int B, int M, int N, int R, cudaStream_t st);

@@ -6,9 +6,22 @@
 
 namespace vdf {
 
+// DDF 5x5 at p = 1/4 (exact or chromaticity terms) runs with score slots
+// (TileCfg::SQ = 1): the selection decides from the same certified Omega^4
+// scores, formed where the aggregates are emitted (not for the diagnostic
+// score dump, which reads raw aggregates).
+inline bool score_slots_p4(const TileParams &prm, int R, int filter, int dist)
+{
+    return R == 2 && filter == DDF && (dist == EXACT || dist == RGB) && prm.dbg_fe == nullptr &&
+           4.0f * (float)prm.p == 1.0f;
+}
+
 template <int TW, int TH>
 cudaError_t run_fp32_shape(const TileParams &prm, int R, int filter, int dist, cudaStream_t st)
 {
+    if (score_slots_p4(prm, R, filter, dist))
+        return dist == EXACT ? launch_tile<TileCfg<2, DDF, EXACT, false, false, TW, TH, NL2, false, 1>>(prm, st)
+                             : launch_tile<TileCfg<2, DDF, RGB, false, false, TW, TH, NL2, false, 1>>(prm, st);
     auto go = [&](auto r, auto f, auto d) {
         return launch_tile<TileCfg<decltype(r)::value, decltype(f)::value, decltype(d)::value, false, false, TW, TH>>(
             prm, st);

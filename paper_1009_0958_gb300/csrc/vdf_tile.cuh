@@ -51,7 +51,8 @@ struct TileParams {
     double T;
 };
 
-template <int R_, int FILTER_, int DIST_, bool FP64_, bool F32IN_, int TW_, int TH_, int NORM_ = NL2, bool ACW_ = false>
+template <int R_, int FILTER_, int DIST_, bool FP64_, bool F32IN_, int TW_, int TH_, int NORM_ = NL2, bool ACW_ = false,
+          int SQ_ = -1>
 struct TileCfg {
     static constexpr int R = R_, FILTER = FILTER_, DIST = DIST_, TW = TW_, TH = TH_, NORM = NORM_;
     static constexpr bool FP64 = FP64_, F32IN = F32IN_;
@@ -59,6 +60,13 @@ struct TileCfg {
     // levels and the switch in the selection
     static constexpr bool ACW = ACW_;
     static_assert(!ACW || (FILTER == DDF && NORM == NL2 && !F32IN), "ACWDDF: uint8 DDF at order 2");
+    // Score slots (FP32 DDF with p = SQ / 4, exact or chromaticity terms):
+    // each (window, member) slot holds the score Omega^4 = SA^SQ SL^(4-SQ),
+    // formed where the aggregates are emitted, instead of the two aggregates
+    // (half the slot bytes, so that two blocks share an SM).  -1: raw slots.
+    static constexpr int SQ = SQ_;
+    static_assert(SQ < 0 || (FILTER == DDF && !FP64 && !F32IN && !ACW && NORM == NL2 && DIST != MINIMAX && SQ <= 4),
+                  "score slots: FP32 uint8 DDF with p = SQ / 4, exact or chromaticity terms");
     static_assert(FILTER != VMF || DIST == EXACT, "VMF has no angular term");
     static_assert(!F32IN || (FILTER != VMF && NORM == NL2), "float input: BVDF / DDF at order 2");
     // VMF at order 1 or infinity: the aggregates are exact integers in both
@@ -78,9 +86,10 @@ struct TileCfg {
     using Pair = typename std::conditional<FP64, double2, float2>::type;
     using PlaneT = typename std::conditional<FILTER == DDF, Pair, Real>::type;
     // per (window, member) slot: the raw aggregates (FP64: later the score in
-    // place); one value for the single-aggregate filters (BVDF, VMF)
-    using HwT = typename std::conditional<FILTER == DDF, typename std::conditional<FP64, double2, float2>::type,
-                                          Real>::type;
+    // place); one value for the single-aggregate filters (BVDF, VMF) and for
+    // score slots
+    using HwT = typename std::conditional<FILTER == DDF && SQ < 0,
+                                          typename std::conditional<FP64, double2, float2>::type, Real>::type;
     static constexpr size_t PIX_BYTES = sizeof(Pix) * CH * PXW;
     static constexpr size_t AUX_BYTES = AUX ? (sizeof(Aux) * CH * PXW + 15) / 16 * 16 : 0;
     // FP32: packed RGB key per pixel for the identical-vector test
@@ -575,6 +584,21 @@ __device__ __forceinline__ void phase32(const typename C::Pix *pix, const Aux *a
     __syncthreads();
 }
 
+// What an FP32 slot holds: the aggregates, or for score slots the score
+// Omega^4 formed from them (the chromaticity terms through Eq. (10) first),
+// with the same operations the selection applies to raw aggregates.
+template <class C>
+__device__ __forceinline__ typename C::HwT slot_value(const typename C::PlaneT &a)
+{
+    if constexpr (C::SQ >= 0) {
+        float sa = a.x;
+        if constexpr (C::DIST == RGB) sa = fmaf(kSlope32, sa, (float)C::NW * kOffset32);
+        return pow4_product<C::SQ>(sa, a.y);
+    } else {
+        return a;
+    }
+}
+
 // The FP32 aggregates of this thread's pixel p, each written to its
 // (window, member) slot of hw when final (windows inside the tile and image).
 template <class C, int... D>
@@ -618,7 +642,7 @@ __device__ __forceinline__ void all_slices32(std::integer_sequence<int, D...>, c
     auto emit = [&](int ey, int ex, const PT &a) {
         if (valid & (1u << ((ey + R) * W + (ex + R)))) {
             const int slot = ((cy - ey - R) * C::TW + (cx - ex - R)) * C::NW + (ey + R) * C::W + (ex + R);
-            hw[slot] = a;
+            hw[slot] = slot_value<C>(a);
         }
     };
     PT st[2 * R][C::W];
@@ -990,7 +1014,9 @@ __device__ __forceinline__ void select_and_store(const TileParams &prm, int b, i
         }
     } else {
         int quarter = -1;
-        if constexpr (C::FILTER == DDF) {
+        if constexpr (C::SQ >= 0) {
+            quarter = C::SQ;   // score slots: p = SQ / 4 (the launcher's choice)
+        } else if constexpr (C::FILTER == DDF) {
             const float p4 = 4.0f * (float)prm.p;
             if (p4 == rintf(p4)) quarter = (int)p4;
         }
@@ -1034,12 +1060,17 @@ __device__ __forceinline__ void select_and_store(const TileParams &prm, int b, i
                         g[k] = pow4_product<decltype(a)::value>(sa, slot_l(f[k]));
                     }
                 };
-                switch (quarter) {
-                case 0: fill(std::integral_constant<int, 0>{}); break;
-                case 1: fill(std::integral_constant<int, 1>{}); break;
-                case 2: fill(std::integral_constant<int, 2>{}); break;
-                case 3: fill(std::integral_constant<int, 3>{}); break;
-                default: fill(std::integral_constant<int, 4>{}); break;
+                if constexpr (C::SQ >= 0) {
+#pragma unroll
+                    for (int k = 0; k < NW; ++k) g[k] = f[k];   // Omega^4, formed at emission
+                } else {
+                    switch (quarter) {
+                    case 0: fill(std::integral_constant<int, 0>{}); break;
+                    case 1: fill(std::integral_constant<int, 1>{}); break;
+                    case 2: fill(std::integral_constant<int, 2>{}); break;
+                    case 3: fill(std::integral_constant<int, 3>{}); break;
+                    default: fill(std::integral_constant<int, 4>{}); break;
+                    }
                 }
             }
             // The near set {g - E <= min (g + E)} is {g <= gmin (1 + erel) / (1 - erel)}.
@@ -1281,7 +1312,7 @@ __device__ __forceinline__ void tile_rest(const TileParams &prm, int b, int x0, 
     //    then the selection, one thread per output pixel (the FP32 selection
     //    scores its own window in registers)
     bool score_all = C::FP64;
-    if constexpr (!C::FP64) score_all = prm.dbg_fe != nullptr;
+    if constexpr (!C::FP64 && C::SQ < 0) score_all = prm.dbg_fe != nullptr;   // (never launched with score slots)
     if (score_all) {
         score_slots<C, NTL>(prm, b, x0, y0, tid, hw);
         __syncthreads();

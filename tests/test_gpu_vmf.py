@@ -45,7 +45,7 @@ def run(V, img, win, filter, p, order, prec, agg=False):
 def images():
     from paper_1009_0958_gb300 import synth
     rng = np.random.default_rng(5)
-    # several 32x16 / 16x16 tiles plus ragged tails
+    # several tiles of every shape plus ragged tails
     yield "rect20", synth.make_image(70, 101, 1, 0.20, rectangles=12)[1]
     yield "field10", synth.make_image(53, 77, 2, 0.10)[1]
     yield "small_range", rng.integers(0, 4, (41, 67, 3)).astype(np.uint8)   # many exact ties
