@@ -310,6 +310,12 @@ int vdf_filter_noalloc(const uint8_t *img, int M, int N, int win, int filter, do
  * image is filtered; out / index_out receive valid results).
  * vdf_get_tuned_shape / vdf_set_tuned_shape read or restore table entries
  * (for example from a cache file).  The paper has no counterpart.
+ * The DDF 5x5 at p = 1/4 with the exact or chromaticity terms runs a kernel
+ * of its own (score slots: each (window, member) slot holds the score, so
+ * smaller tiles fit two blocks per SM) and has its own table entries:
+ * vdf_autotune at that p records into them, vdf_get_tuned_shape_p(..., p)
+ * reads the entry used at exponent p, vdf_get_tuned_shape reads the entry of
+ * the other exponents, and vdf_set_tuned_shape sets both.
  */
 int vdf_num_tile_shapes(void);
 int vdf_tile_shape(int shape, int *tile_w, int *tile_h);
@@ -317,6 +323,7 @@ int vdf_autotune(const uint8_t *img, int M, int N, int win, int filter, double p
                  uint8_t *out, int8_t *index_out, void *workspace, size_t workspace_bytes, int reps, void *stream,
                  int *best_shape, float *best_ms);
 int vdf_get_tuned_shape(int win, int filter, int dist_mode);
+int vdf_get_tuned_shape_p(int win, int filter, int dist_mode, double p);
 int vdf_set_tuned_shape(int win, int filter, int dist_mode, int shape);
 
 /*

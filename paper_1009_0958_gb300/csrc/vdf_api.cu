@@ -64,16 +64,29 @@ int num_sms()
 // different SMs, whose FP64 pipes bound the recheck.
 int recheck_blocks() { return num_sms() * 16; }
 
-// Tile shape of the FP32 kernel per (window, filter, distance mode): shape 0
-// until vdf_autotune or vdf_set_tuned_shape records another.
+// Tile shape of the FP32 kernel per (window, filter, distance mode, slot
+// kind): shape 0 until vdf_autotune or vdf_set_tuned_shape records another.
+// Kind 1 is the score-slot kernel (DDF 5x5 at p = 1/4), whose best shape
+// differs from the raw-slot kernels' of the same configuration.
 std::mutex g_tune_mutex;
-int g_tuned[2][3][3] = {};
+int g_tuned[2][3][3][2] = {};
 
-int tuned_shape(int win, int filter, int dist)
+int tuned_shape(int win, int filter, int dist, int kind = 0)
 {
     if (win != 3 && win != 5) return 0;   // the 7x7 window has no tile shapes
     std::lock_guard<std::mutex> lock(g_tune_mutex);
-    return g_tuned[win / 2 - 1][filter][dist];
+    return g_tuned[win / 2 - 1][filter][dist][kind];
+}
+
+int slot_kind(int win, int filter, int dist, int norm, double p)
+{
+    return vdf::uses_score_slots(win / 2, filter, dist, norm, p) ? 1 : 0;
+}
+
+void record_tuned_shape(int win, int filter, int dist, int kind, int shape)
+{
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    g_tuned[win / 2 - 1][filter][dist][kind] = shape;
 }
 
 // Kernel dispatch by filter kind and Minkowski order (internal code): the
@@ -210,7 +223,8 @@ static int fp32_pass_norm(const uint8_t *img, int M, int N, int win, int filter,
 {
     if (!valid_common(M, N, win, filter, p, dist_mode, minimax_q, VDF_PREC_FP32_RECHECK)) return VDF_E_INVALID;
     return fp32_pass_shape(img, M, N, win, filter, p, dist_mode, minimax_q, out, index_out, workspace,
-                           workspace_bytes, tuned_shape(win, filter, dist_mode), stream, norm);
+                           workspace_bytes, tuned_shape(win, filter, dist_mode, slot_kind(win, filter, dist_mode, norm, p)),
+                           stream, norm);
 }
 
 static int fp64_recheck_norm(const uint8_t *img, int M, int N, int win, int filter, double p, int dist_mode,
@@ -472,15 +486,29 @@ int vdf_get_tuned_shape(int win, int filter, int dist_mode)
     return tuned_shape(win, filter, filter == VDF_VMF ? VDF_DIST_EXACT : dist_mode);
 }
 
+int vdf_get_tuned_shape_p(int win, int filter, int dist_mode, double p)
+{
+    if ((win != 3 && win != 5) || filter < 0 || filter > 2 || dist_mode < 0 || dist_mode > 2) return VDF_E_INVALID;
+    if (filter == VDF_VMF) dist_mode = VDF_DIST_EXACT;
+    return tuned_shape(win, filter, dist_mode, slot_kind(win, filter, dist_mode, vdf::NL2, p));
+}
+
 int vdf_set_tuned_shape(int win, int filter, int dist_mode, int shape)
 {
     if ((win != 3 && win != 5) || filter < 0 || filter > 2 || dist_mode < 0 || dist_mode > 2) return VDF_E_INVALID;
     if (shape < 0 || shape >= vdf::kNumShapes32) return VDF_E_INVALID;
     if (filter == VDF_VMF) dist_mode = VDF_DIST_EXACT;   // one entry: the VMF has no angular term
-    std::lock_guard<std::mutex> lock(g_tune_mutex);
-    g_tuned[win / 2 - 1][filter][dist_mode] = shape;
+    for (int kind = 0; kind < 2; ++kind) record_tuned_shape(win, filter, dist_mode, kind, shape);
     return VDF_OK;
 }
+
+}  // extern "C"
+
+namespace vdf {
+int tuned_shape_p(int win, int filter, int dist, double p) { return vdf_get_tuned_shape_p(win, filter, dist, p); }
+}  // namespace vdf
+
+extern "C" {
 
 int vdf_autotune(const uint8_t *img, int M, int N, int win, int filter, double p, int dist_mode, int minimax_q,
                  uint8_t *out, int8_t *index_out, void *workspace, size_t workspace_bytes, int reps, void *stream,
@@ -523,7 +551,7 @@ int vdf_autotune(const uint8_t *img, int M, int N, int win, int filter, double p
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc != VDF_OK) return rc;
-    vdf_set_tuned_shape(win, filter, dist_mode, bs);
+    record_tuned_shape(win, filter, dist_mode, slot_kind(win, filter, dist_mode, vdf::NL2, p), bs);
     // leave a complete result in out / index_out
     rc = vdf_fp32_pass(img, M, N, win, filter, p, dist_mode, minimax_q, out, index_out, workspace, workspace_bytes,
                        stream);

@@ -175,7 +175,7 @@ int vdf_plan_create(vdf_plan **plan, const vdf_image_desc *descs, int count, int
             delete pl;
             return VDF_E_INVALID;
         }
-        const int shape = vdf_get_tuned_shape(d.win, d.filter, dist_mode);
+        const int shape = vdf::tuned_shape_p(d.win, d.filter, dist_mode, d.p);
         vdf::BatchDesc bd{};
         bd.img = d.img;
         bd.out = d.out;
@@ -185,8 +185,7 @@ int vdf_plan_create(vdf_plan **plan, const vdf_image_desc *descs, int count, int
         bd.tiles_x = (d.N + vdf::kShapes32[shape].tw - 1) / vdf::kShapes32[shape].tw;
         bd.cfg = ((d.win / 2 - 1) * 2 + d.filter) * vdf::kNumShapes32 + shape;
         // DDF 5x5 at p = 1/4 (exact or chromaticity terms): the score-slot kernels
-        if (d.win == 5 && d.filter == VDF_DDF && dist_mode != VDF_DIST_MINIMAX && 4.0f * (float)d.p == 1.0f)
-            bd.cfg = vdf::kScoreCfg0 + shape;
+        if (vdf::uses_score_slots(d.win / 2, d.filter, dist_mode, vdf::NL2, d.p)) bd.cfg = vdf::kScoreCfg0 + shape;
         bd.p = d.p;
         all.push_back(bd);
     }

@@ -21,6 +21,15 @@ constexpr int kNumShapes32 = 4;
 // (BVDF, VMF, and the DDF's score slots at p = 1/4).
 inline constexpr TileShape kShapes32[kNumShapes32] = {{32, 16}, {32, 8}, {24, 12}, {28, 16}};
 cudaError_t run_fp32(const TileParams &prm, int R, int filter, int dist, int shape, cudaStream_t st);
+// Whether the FP32 kernel of a configuration keeps score slots (TileCfg::SQ):
+// the DDF 5x5 at p = 1/4 with the exact or chromaticity terms, order 2.
+// Such configurations have their own tile-shape table entries.
+inline bool uses_score_slots(int R, int filter, int dist, int norm, double p)
+{
+    return R == 2 && filter == DDF && (dist == EXACT || dist == RGB) && norm == NL2 && 4.0f * (float)p == 1.0f;
+}
+// The tuned tile shape of a configuration at DDF exponent p (order 2).
+int tuned_shape_p(int win, int filter, int dist, double p);
 // Gradient gather of the float32 path.
 cudaError_t run_backward(const float *gy, const int8_t *idx, float *gx, int B, int M, int N, int R, cudaStream_t st);
 // FP32 certified tile kernel for float32 B x 3 x M x N input (exact mode, 32x16 tiles).

@@ -12,8 +12,7 @@ namespace vdf {
 // score dump, which reads raw aggregates).
 inline bool score_slots_p4(const TileParams &prm, int R, int filter, int dist)
 {
-    return R == 2 && filter == DDF && (dist == EXACT || dist == RGB) && prm.dbg_fe == nullptr &&
-           4.0f * (float)prm.p == 1.0f;
+    return uses_score_slots(R, filter, dist, NL2, prm.p) && prm.dbg_fe == nullptr;
 }
 
 template <int TW, int TH>

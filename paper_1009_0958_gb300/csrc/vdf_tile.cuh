@@ -309,9 +309,15 @@ __device__ __forceinline__ typename C::PlaneT pair_term(const typename C::Pix &a
 template <class C>
 __device__ __forceinline__ void add_term(typename C::PlaneT &x, const typename C::PlaneT &y)
 {
-    if constexpr (C::FILTER == DDF) {
-        // two scalar adds: the packed FP32 add measured slower here (longer
-        // latency in these dependent sum chains, no throughput gain on GB300)
+    if constexpr (C::FILTER == DDF && !C::FP64) {
+        // FP32 (angular, L2) pair: one packed add, each lane rounded as a
+        // scalar add.rn.ftz (the FP32 units are built flush-to-zero), so the
+        // sums are bit-identical to two scalar adds in one issue slot
+        asm("{\n\t.reg .b64 ra, rb;\n\tmov.b64 ra, {%0, %1};\n\tmov.b64 rb, {%2, %3};\n\t"
+            "add.rn.ftz.f32x2 ra, ra, rb;\n\tmov.b64 {%0, %1}, ra;\n\t}"
+            : "+f"(x.x), "+f"(x.y)
+            : "f"(y.x), "f"(y.y));
+    } else if constexpr (C::FILTER == DDF) {
         x.x += y.x;
         x.y += y.y;
     } else {

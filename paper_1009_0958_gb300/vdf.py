@@ -345,9 +345,10 @@ def _tune_fns(L):
         L.vdf_autotune.argtypes = [P, i, i, i, i, d, i, i, P, P, P, sz, i, P, P, P]
         L.vdf_tile_shape.argtypes = [i, P, P]
         L.vdf_get_tuned_shape.argtypes = [i, i, i]
+        L.vdf_get_tuned_shape_p.argtypes = [i, i, i, d]
         L.vdf_set_tuned_shape.argtypes = [i, i, i, i]
-        for f in ("vdf_autotune", "vdf_tile_shape", "vdf_get_tuned_shape", "vdf_set_tuned_shape",
-                  "vdf_num_tile_shapes"):
+        for f in ("vdf_autotune", "vdf_tile_shape", "vdf_get_tuned_shape", "vdf_get_tuned_shape_p",
+                  "vdf_set_tuned_shape", "vdf_num_tile_shapes"):
             getattr(L, f).restype = i
     return L
 
@@ -379,8 +380,12 @@ def autotune(img: torch.Tensor, win=5, filter="ddf", p=0.25, dist="exact", q=4, 
     return s.value, ms.value
 
 
-def tuned_shape(win, filter="ddf", dist="exact") -> int:
-    return int(_tune_fns(lib()).vdf_get_tuned_shape(win, _code(FILTERS, filter), _code(DISTS, dist)))
+def tuned_shape(win, filter="ddf", dist="exact", p=None) -> int:
+    """The tuned tile shape; with p, the entry used at that DDF exponent."""
+    L = _tune_fns(lib())
+    if p is None:
+        return int(L.vdf_get_tuned_shape(win, _code(FILTERS, filter), _code(DISTS, dist)))
+    return int(L.vdf_get_tuned_shape_p(win, _code(FILTERS, filter), _code(DISTS, dist), float(p)))
 
 
 def set_tuned_shape(win, filter, dist, shape: int):

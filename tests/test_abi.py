@@ -119,6 +119,24 @@ def test_window_7_limits_on_host(L, B):
     assert L.vdf_set_tuned_shape(7, 1, 0, 0) == -1 and L.vdf_get_tuned_shape(7, 1, 0) == -1
 
 
+def test_tuned_shape_table_kinds(L):
+    """The DDF 5x5 at p = 1/4 (exact, Method 2) has its own table entry (score
+    slots); vdf_set_tuned_shape writes both entries; Method 1, other
+    exponents, 3x3 and the BVDF read the raw-slot entry."""
+    L.vdf_get_tuned_shape_p.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double]
+    L.vdf_get_tuned_shape_p.restype = ctypes.c_int
+    try:
+        for dist in (0, 1, 2):
+            assert L.vdf_set_tuned_shape(5, 1, dist, 3) == 0
+            assert L.vdf_get_tuned_shape(5, 1, dist) == 3
+            for p in (0.25, 0.3, 0.5):
+                assert L.vdf_get_tuned_shape_p(5, 1, dist, p) == 3
+        assert L.vdf_get_tuned_shape_p(7, 1, 0, 0.25) == -1 and L.vdf_get_tuned_shape_p(5, 3, 0, 0.25) == -1
+    finally:
+        for dist in (0, 1, 2):
+            L.vdf_set_tuned_shape(5, 1, dist, 0)
+
+
 def test_aliasing_and_workspace_checks(L, B):
     p = B[0]
     assert L.vdf_filter(p, 8, 8, 3, 0, 0.5, 0, 4, 0, p, None, None, None, 0, None) == -1      # out == img

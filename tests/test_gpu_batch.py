@@ -130,9 +130,14 @@ def test_every_tile_shape_gives_the_same_result(V, win, filter):
         V.set_tuned_shape(win, filter, "exact", s)
         o, i = V.filter(x, win, filter, 0.25, precision="fp32")
         assert torch.equal(o, ref[0]) and torch.equal(i, ref[1])
+    last = len(V.tile_shapes()) - 1
     shape, ms = V.autotune(x, win, filter, 0.25, reps=3)
     assert 0 <= shape < len(V.tile_shapes()) and ms > 0
-    assert V.tuned_shape(win, filter) == shape
+    assert V.tuned_shape(win, filter, p=0.25) == shape
+    # the DDF 5x5 at p = 1/4 (score slots) has its own entry: the other
+    # exponents keep the shape set before
+    assert V.tuned_shape(win, filter) == (last if (win, filter) == (5, "ddf") else shape)
+    V.set_tuned_shape(win, filter, "exact", 0)
 
 
 def test_plan_rejects_bad_descriptors(V):
