@@ -1,5 +1,6 @@
 """Fit the float32 polynomial atan(t) = t * Q(t^2), t in [0, 1], used by the
-FP32 exact-angle term in vdf_internal.cuh (kAtanQ).
+FP32 exact-angle term in vdf_internal.cuh (atan_q; 7 coefficients, Q of
+degree 6).
 
 Lawson's iteration (iteratively reweighted least squares) on a dense grid
 drives the maximum *relative* error to its minimax value; the coefficients
@@ -38,7 +39,7 @@ def float32_eval_error(c32):
 
 
 if __name__ == "__main__":
-    n = int(sys.argv[1]) if len(sys.argv) > 1 else 8
+    n = int(sys.argv[1]) if len(sys.argv) > 1 else 7
     c32 = fit(n).astype(np.float32)
     print("constexpr float kAtanQ[%d] = {%s};" % (n, ", ".join("%.8gf" % v for v in c32)))
     print("max relative error of the float32 evaluation: %.2f ulp (u = 2^-24)" % float32_eval_error(c32))

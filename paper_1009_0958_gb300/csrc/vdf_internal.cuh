@@ -92,22 +92,28 @@ constexpr float kOffset32 = 0.027664f;
 constexpr double kHalfPi64 = 1.5707963267948966;   // nearest double to pi/2
 constexpr float kHalfPi32 = 1.57079637f;           // nearest float to pi/2
 
-// atan(t) = t * Q(t^2) on [0, 1]: minimax fit for relative error (script
-// gen_atan_poly.py next to this file); float32 Horner evaluation error is
-// below 3.6 ulp of the result over the whole range.
+// atan(t) = t * Q(t^2) on [0, 1], Q of degree 6: minimax fit for relative
+// error (script gen_atan_poly.py next to this file); float32 Horner
+// evaluation error is below 12.8 ulp of the result over the whole range.
 // Coefficient k as a constant expression (immediate operands, nothing
 // loaded from memory).
+constexpr int kAtanDeg = 6;
 __host__ __device__ constexpr float atan_q(int k)
 {
-    return k == 0   ? 0.99999988f
-           : k == 1 ? -0.3333199f
-           : k == 2 ? 0.19969724f
-           : k == 3 ? -0.14019482f
-           : k == 4 ? 0.099142946f
-           : k == 5 ? -0.059486423f
-           : k == 6 ? 0.02425243f
-                    : -0.0046932846f;
+    return k == 0   ? 0.99999934f
+           : k == 1 ? -0.33326516f
+           : k == 2 ? 0.19881482f
+           : k == 3 ? -0.13487193f
+           : k == 4 ? 0.08387123f
+           : k == 5 ? -0.037013046f
+                    : 0.007863394f;
 }
+
+// Relative bounds of the FP32 angle term in units of u = 2^-24 (before the
+// safety factor): integer input (angle32: the reciprocal square root, the
+// Lagrange c2, the products and 12.8u of polynomial) and float input
+// (angle32f: 8u more for its normalised products).
+constexpr float kAngleU = 26.0f, kAngleFU = 34.0f;
 
 // ----------------------------------------------------- FP64 pair terms ----
 // Inputs are the integer RGB values of two pixels with n2 = |x|^2 in .w.
@@ -267,16 +273,16 @@ __device__ __forceinline__ float angle_core(float c2, float Dh, float guard)
     // t = min(tan, cot) = min(sqrt(c2)/d, d/sqrt(c2)) = min(c2, d^2) / sqrt(c2 d^2)
     const float t = fminf(c2, Dh) * rs;
     const float s = t * t;
-    float v = atan_q(7);
+    float v = atan_q(kAtanDeg);
 #pragma unroll
-    for (int k = 6; k >= 0; --k) v = fmaf(v, s, atan_q(k));
+    for (int k = kAtanDeg - 1; k >= 0; --k) v = fmaf(v, s, atan_q(k));
     const float a = t * v;
     // c2 >= d^2: theta >= 45 deg (also a zero vector: both 0, theta = pi/2)
     return (c2 >= Dh) ? (kHalfPi32 - a) : a;
 }
 
 // Eq. (2) angle in FP32: theta = atan2(sqrt(c2), d) via t = min(tan, cot).
-// Relative error <= 16u (rsqrt 2 ulp, the Lagrange c2, the polynomial).
+// Relative error <= kAngleU u (rsqrt 2 ulp, the Lagrange c2, the polynomial).
 __device__ __forceinline__ float angle32(const PairInts &r)
 {
     // c2 * d^2 is 0 or >= 1 (integers), so adding 1e-30 only guards the zero
@@ -349,7 +355,7 @@ __device__ __forceinline__ float det2(float a, float b, float c, float d)
 // Eq. (2) angle of two normalised safe pixels.  d (three non-negative
 // products, FMA chain): <= 3u; each cross component <= 2u (Kahan), so
 // |x x y|^2 <= 6u and d^2 <= 7u; the rest as angle32.  Relative error
-// <= 24u (doubled by the bound's safety factor), plus an absolute 2^-58
+// <= kAngleFU u (doubled by the bound's safety factor), plus an absolute 2^-58
 // where a tiny product underflows; the guard 2^-120 lies below c2 d^2 except
 // for angles within 2^-58 of 0 or pi/2.
 __device__ __forceinline__ float angle32f(const float4 a, const float4 b)

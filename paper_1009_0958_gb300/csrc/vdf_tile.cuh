@@ -151,7 +151,7 @@ __device__ __forceinline__ int select64(F f)
 }
 
 // FP32 score and certified bound.  Relative error bounds (in units of
-// u = 2^-24) of the aggregates: angle 16 + 4R (terms + two summation
+// u = 2^-24) of the aggregates: angle kAngleU + 4R (terms + two summation
 // stages), chromaticity 11 + 4R (+2 for Eq. (10)), L2 6 + 4R; Method 1 has
 // an absolute bound 24u per term plus 4R u |SA|.  Bounds are doubled.
 // Omega^4 = SA^a SL^(4-a) for p = a/4, with at most three rounded products.
@@ -174,7 +174,7 @@ template <int R, int DIST, bool F32IN = false>
 __device__ __forceinline__ float pow4_erel(int a)
 {
     constexpr float S = 4.0f * R;
-    constexpr float relA = (DIST == RGB ? 13.0f + S : (F32IN ? 24.0f : 16.0f) + S) * kU;
+    constexpr float relA = (DIST == RGB ? 13.0f + S : (F32IN ? kAngleFU : kAngleU) + S) * kU;
     constexpr float relL = ((F32IN ? 8.0f : 6.0f) + S) * kU;
     return kSafety * (a * relA + (4 - a) * relL + 3.0f * kU);
 }
@@ -184,7 +184,7 @@ __device__ __forceinline__ float2 score32(float sa, float sl, float p, int quart
 {
     constexpr int NW = (2 * R + 1) * (2 * R + 1);
     constexpr float S = 4.0f * R;
-    constexpr float kA = F32IN ? 24.0f : 16.0f, kL = F32IN ? 8.0f : 6.0f;   // term bounds, float / integer input
+    constexpr float kA = F32IN ? kAngleFU : kAngleU, kL = F32IN ? 8.0f : 6.0f;   // term bounds, float / integer input
     if (FILTER == VMF)   // sum of distances: order 2 as the L2 aggregate, orders 1 and infinity exact
         return make_float2(sa, NORM == NL2 ? kSafety * (kL + S) * kU * sa : 0.0f);
     if (FILTER == BVDF) {
@@ -956,7 +956,7 @@ __device__ __forceinline__ int acw_select32(const TileParams &prm, const float4 
         float a, relA = 0.0f, absA = 0.0f;
         if constexpr (DIST == EXACT) {
             a = angle32(r);
-            relA = 16.0f;
+            relA = kAngleU;
         } else if constexpr (DIST == MINIMAX) {
             a = minimax32(r, aux[P(y)], aux[P(CENTRE)], prm.q);
             absA = 24.0f;
@@ -1054,7 +1054,7 @@ __device__ __forceinline__ void select_and_store(const TileParams &prm, int b, i
             } else if constexpr (C::FILTER == BVDF) {
 #pragma unroll
                 for (int k = 0; k < NW; ++k) g[k] = slot_a(f[k]);
-                erel = kSafety * ((C::DIST == RGB ? 11.0f : (C::F32IN ? 24.0f : 16.0f)) + 4.0f * R) * kU;
+                erel = kSafety * ((C::DIST == RGB ? 11.0f : (C::F32IN ? kAngleFU : kAngleU)) + 4.0f * R) * kU;
             } else {
                 // the uniform switch keeps each unrolled loop branch-free
                 erel = pow4_erel<R, C::DIST, C::F32IN>(quarter);

@@ -57,7 +57,7 @@ def test_float_terms_within_bounds(V):
     ang, l2 = ang.cpu().numpy().astype(np.float64), l2.cpu().numpy().astype(np.float64)
     assert not np.isnan(ang).any() and not np.isnan(l2).any()
     th, ref_l2 = exact_terms(pairs)
-    assert np.all(np.abs(ang - th) <= 24 * U * th + 2.0 ** -58)
+    assert np.all(np.abs(ang - th) <= 34 * U * th + 2.0 ** -58)   # kAngleFU
     assert np.all(np.abs(l2 - ref_l2) <= 8 * U * ref_l2 + 2.0 ** -62)
     assert np.all(ang[(pairs[:, :3] == pairs[:, 3:]).all(1) & (pairs[:, :3] != 0).any(1)] == 0.0)
 
