@@ -73,7 +73,7 @@ typedef enum {
     VDF_E_TIMEOUT = -4,     /* reserved, never returned: no kernel of this
                                library waits on the device */
     VDF_E_WORKSPACE = -5,   /* workspace missing or smaller than required */
-    VDF_E_UNSUPPORTED = -6  /* valid request this build does not implement */
+    VDF_E_UNSUPPORTED = -6  /* valid request the library does not implement */
 } vdf_status;
 
 /* Human-readable text of a status code (static storage). */
