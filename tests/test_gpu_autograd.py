@@ -73,6 +73,34 @@ def test_backward_matches_oracle_index_gradient(V, O, win, shape):
     assert np.allclose(got, want, rtol=1e-6, atol=1e-6)
 
 
+@pytest.mark.parametrize("win", [3, 5])
+@pytest.mark.parametrize("shape", [(2, 150, 260), (1, 37, 132), (1, 64, 128), (3, 9, 4), (1, 70, 57)])
+def test_backward_random_index_maps(V, win, shape):
+    """The gradient gather on random index maps, every pixel against a numpy
+    scatter: strips and row segments with ragged tails (the streaming form for
+    widths that are multiples of 4, the staged form otherwise), and bytes
+    outside 0..n-1, which select nothing."""
+    B, M, N = shape
+    rng = np.random.default_rng(M * N + win)
+    n = win * win
+    idx = rng.integers(0, n, (B, M, N)).astype(np.int8)
+    bad = rng.random((B, M, N)) < 0.02
+    idx[bad] = rng.choice(np.array([-1, n, 127], dtype=np.int8), bad.sum())
+    gy = rng.standard_normal((B, 3, M, N)).astype(np.float32)
+    got = V.backward_f32(torch.from_numpy(gy).cuda(), torch.from_numpy(idx).cuda(), win).cpu().numpy()
+    R = win // 2
+    want = np.zeros((B, 3, M, N), np.float64)
+    yy, xx = np.meshgrid(np.arange(M), np.arange(N), indexing="ij")
+    for b in range(B):
+        i = idx[b].astype(np.int64)
+        ok = (i >= 0) & (i < n)
+        sy = np.clip(yy + i // win - R, 0, M - 1)[ok]
+        sx = np.clip(xx + i % win - R, 0, N - 1)[ok]
+        for c in range(3):
+            np.add.at(want[b, c], (sy, sx), gy[b, c][ok].astype(np.float64))
+    assert np.allclose(got, want, rtol=1e-5, atol=1e-5)
+
+
 def test_backward_deterministic(V):
     x = torch.from_numpy(batch(2, 64, 80, 11)).cuda()
     y, idx = V.filter_f32(x, 3, "ddf", 0.25)
