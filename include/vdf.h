@@ -310,12 +310,13 @@ int vdf_filter_noalloc(const uint8_t *img, int M, int N, int win, int filter, do
  * image is filtered; out / index_out receive valid results).
  * vdf_get_tuned_shape / vdf_set_tuned_shape read or restore table entries
  * (for example from a cache file).  The paper has no counterpart.
- * The DDF 5x5 at p = 1/4 with the exact or chromaticity terms runs a kernel
- * of its own (score slots: each (window, member) slot holds the score, so
- * smaller tiles fit two blocks per SM) and has its own table entries:
- * vdf_autotune at that p records into them, vdf_get_tuned_shape_p(..., p)
- * reads the entry used at exponent p, vdf_get_tuned_shape reads the entry of
- * the other exponents, and vdf_set_tuned_shape sets both.
+ * The DDF 5x5 at p = 1/4, 1/2 or 3/4 with the exact or chromaticity terms
+ * runs kernels of its own (score slots: each (window, member) slot holds the
+ * score, so smaller tiles fit two blocks per SM) and has table entries of its
+ * own for each of the three exponents: vdf_autotune at such a p records into
+ * that p's entry, vdf_get_tuned_shape_p(..., p) reads the entry used at
+ * exponent p, vdf_get_tuned_shape reads the entry of the other exponents, and
+ * vdf_set_tuned_shape sets them all.
  */
 int vdf_num_tile_shapes(void);
 int vdf_tile_shape(int shape, int *tile_w, int *tile_h);

@@ -66,10 +66,11 @@ int recheck_blocks() { return num_sms() * 16; }
 
 // Tile shape of the FP32 kernel per (window, filter, distance mode, slot
 // kind): shape 0 until vdf_autotune or vdf_set_tuned_shape records another.
-// Kind 1 is the score-slot kernel (DDF 5x5 at p = 1/4), whose best shape
-// differs from the raw-slot kernels' of the same configuration.
+// Kinds 1..3 are the score-slot kernels (DDF 5x5 at p = kind / 4), whose
+// best shape differs from the raw-slot kernels' of the same configuration.
+constexpr int kSlotKinds = 4;
 std::mutex g_tune_mutex;
-int g_tuned[2][3][3][2] = {};
+int g_tuned[2][3][3][kSlotKinds] = {};
 
 int tuned_shape(int win, int filter, int dist, int kind = 0)
 {
@@ -80,7 +81,7 @@ int tuned_shape(int win, int filter, int dist, int kind = 0)
 
 int slot_kind(int win, int filter, int dist, int norm, double p)
 {
-    return vdf::uses_score_slots(win / 2, filter, dist, norm, p) ? 1 : 0;
+    return vdf::score_slot_exponent(win / 2, filter, dist, norm, p);
 }
 
 void record_tuned_shape(int win, int filter, int dist, int kind, int shape)
@@ -498,7 +499,7 @@ int vdf_set_tuned_shape(int win, int filter, int dist_mode, int shape)
     if ((win != 3 && win != 5) || filter < 0 || filter > 2 || dist_mode < 0 || dist_mode > 2) return VDF_E_INVALID;
     if (shape < 0 || shape >= vdf::kNumShapes32) return VDF_E_INVALID;
     if (filter == VDF_VMF) dist_mode = VDF_DIST_EXACT;   // one entry: the VMF has no angular term
-    for (int kind = 0; kind < 2; ++kind) record_tuned_shape(win, filter, dist_mode, kind, shape);
+    for (int kind = 0; kind < kSlotKinds; ++kind) record_tuned_shape(win, filter, dist_mode, kind, shape);
     return VDF_OK;
 }
 

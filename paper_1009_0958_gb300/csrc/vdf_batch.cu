@@ -185,7 +185,8 @@ int vdf_plan_create(vdf_plan **plan, const vdf_image_desc *descs, int count, int
         bd.tiles_x = (d.N + vdf::kShapes32[shape].tw - 1) / vdf::kShapes32[shape].tw;
         bd.cfg = ((d.win / 2 - 1) * 2 + d.filter) * vdf::kNumShapes32 + shape;
         // DDF 5x5 at p = 1/4 (exact or chromaticity terms): the score-slot kernels
-        if (vdf::uses_score_slots(d.win / 2, d.filter, dist_mode, vdf::NL2, d.p)) bd.cfg = vdf::kScoreCfg0 + shape;
+        if (const int a = vdf::score_slot_exponent(d.win / 2, d.filter, dist_mode, vdf::NL2, d.p))
+            bd.cfg = vdf::kScoreCfg0 + (a - 1) * vdf::kNumShapes32 + shape;
         bd.p = d.p;
         all.push_back(bd);
     }

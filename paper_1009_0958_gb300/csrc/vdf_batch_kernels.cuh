@@ -19,7 +19,7 @@ struct BatchDesc {
     int tiles_x;
     int tile_base;   // first work item of this image within its group
     int pix_base;    // first batch pixel offset of this image (ascending over the descriptor array)
-    int cfg;         // ((win/2 - 1) * 2 + filter) * kNumShapes32 + shape; kScoreCfg0 + shape: DDF 5x5, p = 1/4
+    int cfg;         // ((win/2 - 1) * 2 + filter) * kNumShapes32 + shape; DDF 5x5 at p = a/4: kScoreCfg0 + (a-1) * kNumShapes32 + shape
     double p;
 };
 
@@ -35,10 +35,10 @@ struct BatchParams {
     int q;
 };
 
-// Configurations: window x filter x tile shape, then DDF 5x5 at p = 1/4
-// with score slots (exact and chromaticity terms) in every shape.
+// Configurations: window x filter x tile shape, then the DDF 5x5 at p = a/4
+// (a = 1, 2, 3) with score slots (exact and chromaticity terms) in every shape.
 constexpr int kScoreCfg0 = 2 * 2 * kNumShapes32;
-constexpr int kNumCfgs = kScoreCfg0 + kNumShapes32;
+constexpr int kNumCfgs = kScoreCfg0 + 3 * kNumShapes32;
 
 // The configuration a kernel is instantiated for: Method 1 has no score-slot
 // configurations (its plans never use them), so those entries reuse the raw
@@ -46,7 +46,7 @@ constexpr int kNumCfgs = kScoreCfg0 + kNumShapes32;
 template <int DIST, int CFG>
 constexpr int canonical_cfg()
 {
-    return (CFG >= kScoreCfg0 && DIST == MINIMAX) ? CFG - kNumShapes32 : CFG;
+    return (CFG >= kScoreCfg0 && DIST == MINIMAX) ? kScoreCfg0 - kNumShapes32 + CFG % kNumShapes32 : CFG;
 }
 
 template <int DIST, int CFG>
@@ -57,7 +57,7 @@ struct BCfg {
     static constexpr int FILTER = SCORE ? DDF : (CFG / kNumShapes32) % 2;
     static constexpr int R = SCORE ? 2 : CFG / (2 * kNumShapes32) + 1;
     using C = TileCfg<R, FILTER, DIST, false, false, kShapes32[SHAPE].tw, kShapes32[SHAPE].th, NL2, false,
-                      SCORE ? 1 : -1>;
+                      SCORE ? 1 + (CFG - kScoreCfg0) / kNumShapes32 : -1>;
 };
 
 // The persistent tile kernel of one configuration.
@@ -203,7 +203,7 @@ __global__ void __launch_bounds__(32 * kRecheckWarps) batch_recheck_kernel(const
         }
         const BatchDesc d = bp.desc[lo];
         const int lin = ent.x - d.pix_base;
-        const int rf = d.cfg / kNumShapes32;   // (R - 1) * 2 + filter; 4: DDF 5x5 with score slots
+        const int rf = d.cfg / kNumShapes32;   // (R - 1) * 2 + filter; 4..6: DDF 5x5 with score slots
         const unsigned mask = (unsigned)ent.y;
         switch (rf) {
         case 0: recheck_pixel<1, BVDF, DIST>(d.img, d.M, d.N, lin, mask, d.out, d.idx, d.p, bp.q, base, lane); break;

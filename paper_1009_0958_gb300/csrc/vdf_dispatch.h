@@ -21,12 +21,16 @@ constexpr int kNumShapes32 = 4;
 // (BVDF, VMF, and the DDF's score slots at p = 1/4).
 inline constexpr TileShape kShapes32[kNumShapes32] = {{32, 16}, {32, 8}, {24, 12}, {28, 16}};
 cudaError_t run_fp32(const TileParams &prm, int R, int filter, int dist, int shape, cudaStream_t st);
-// Whether the FP32 kernel of a configuration keeps score slots (TileCfg::SQ):
-// the DDF 5x5 at p = 1/4 with the exact or chromaticity terms, order 2.
-// Such configurations have their own tile-shape table entries.
-inline bool uses_score_slots(int R, int filter, int dist, int norm, double p)
+// The exponent a of the FP32 kernel's score slots (TileCfg::SQ: each slot
+// holds Omega^4 = SA^a SL^(4-a)), or 0 for raw slots: the DDF 5x5 with the
+// exact or chromaticity terms, order 2, at p = a / 4 for a = 1, 2, 3 (p = 1/2
+// orders like the plain product of Eq. (3)).  Such configurations have tile-
+// shape table entries of their own.
+inline int score_slot_exponent(int R, int filter, int dist, int norm, double p)
 {
-    return R == 2 && filter == DDF && (dist == EXACT || dist == RGB) && norm == NL2 && 4.0f * (float)p == 1.0f;
+    if (R != 2 || filter != DDF || (dist != EXACT && dist != RGB) || norm != NL2) return 0;
+    const float p4 = 4.0f * (float)p;
+    return (p4 == 1.0f || p4 == 2.0f || p4 == 3.0f) ? (int)p4 : 0;
 }
 // The tuned tile shape of a configuration at DDF exponent p (order 2).
 int tuned_shape_p(int win, int filter, int dist, double p);

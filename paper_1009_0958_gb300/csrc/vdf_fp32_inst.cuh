@@ -6,21 +6,26 @@
 
 namespace vdf {
 
-// DDF 5x5 at p = 1/4 (exact or chromaticity terms) runs with score slots
-// (TileCfg::SQ = 1): the selection decides from the same certified Omega^4
-// scores, formed where the aggregates are emitted (not for the diagnostic
-// score dump, which reads raw aggregates).
-inline bool score_slots_p4(const TileParams &prm, int R, int filter, int dist)
+// DDF 5x5 at p = 1/4, 1/2 or 3/4 (exact or chromaticity terms) runs with
+// score slots (TileCfg::SQ = 4p): the selection decides from the same
+// certified Omega^4 scores, formed where the aggregates are emitted (not for
+// the diagnostic score dump, which reads raw aggregates).
+template <int TW, int TH, int A>
+cudaError_t launch_score_slots(const TileParams &prm, int dist, cudaStream_t st)
 {
-    return uses_score_slots(R, filter, dist, NL2, prm.p) && prm.dbg_fe == nullptr;
+    return dist == EXACT ? launch_tile<TileCfg<2, DDF, EXACT, false, false, TW, TH, NL2, false, A>>(prm, st)
+                         : launch_tile<TileCfg<2, DDF, RGB, false, false, TW, TH, NL2, false, A>>(prm, st);
 }
 
 template <int TW, int TH>
 cudaError_t run_fp32_shape(const TileParams &prm, int R, int filter, int dist, cudaStream_t st)
 {
-    if (score_slots_p4(prm, R, filter, dist))
-        return dist == EXACT ? launch_tile<TileCfg<2, DDF, EXACT, false, false, TW, TH, NL2, false, 1>>(prm, st)
-                             : launch_tile<TileCfg<2, DDF, RGB, false, false, TW, TH, NL2, false, 1>>(prm, st);
+    switch (prm.dbg_fe ? 0 : score_slot_exponent(R, filter, dist, NL2, prm.p)) {
+    case 1: return launch_score_slots<TW, TH, 1>(prm, dist, st);
+    case 2: return launch_score_slots<TW, TH, 2>(prm, dist, st);
+    case 3: return launch_score_slots<TW, TH, 3>(prm, dist, st);
+    default: break;
+    }
     auto go = [&](auto r, auto f, auto d) {
         return launch_tile<TileCfg<decltype(r)::value, decltype(f)::value, decltype(d)::value, false, false, TW, TH>>(
             prm, st);

@@ -38,7 +38,7 @@ def batch_items(seed, count, hi=300, extra=True):
     for k, (M, N) in enumerate(shapes):
         _, img = synth.make_image(M, N, seed * 1000 + k, 0.15, rectangles=3)
         items.append(dict(img=torch.from_numpy(img).cuda(), win=int(rng.choice([3, 5])),
-                          filter=str(rng.choice(["bvdf", "ddf"])), p=float(rng.choice([0.0, 0.25, 0.5, 1.0]))))
+                          filter=str(rng.choice(["bvdf", "ddf"])), p=float(rng.choice([0.0, 0.25, 0.5, 0.75, 1.0]))))
     return items
 
 

@@ -9,7 +9,8 @@
   and 5x5, exact / Method 1 (q = 4) / Method 2, 20% impulses): both
   precisions against the oracle on every pixel.
 * Every FP32 tile shape in Methods 1 and 2, since the autotuner may pick any
-  of them for those modes.
+  of them for those modes, and every shape of the score-slot kernels (DDF
+  5x5 at p = 1/4, 1/2, 3/4).
 
 Selections are compared bit for bit: member index and RGB.
 """
@@ -114,6 +115,19 @@ def test_tile_shapes_methods_1_and_2(V, O, small_image, shape, win, filter, p, d
     ref = O.filter_u8(small_image, win, filter, p, dist, q)
     out, idx, st = gpu(V, small_image, win, filter, p, dist, q, "fp32", shape=shape)
     V.set_tuned_shape(win, filter, dist, 0)
+    assert_same(out, idx, ref, f"shape {shape}")
+    assert st["overflow"] == 0
+
+
+@pytest.mark.parametrize("shape", [0, 1, 2, 3])
+@pytest.mark.parametrize("p", [0.25, 0.5, 0.75])
+@pytest.mark.parametrize("dist", ["exact", "rgb"])
+def test_score_slot_kernels_every_shape(V, O, small_image, shape, p, dist):
+    """The DDF 5x5 at p = 1/4, 1/2 and 3/4 runs with score slots (Omega^4 per
+    slot) in every tile shape: every pixel equals the oracle."""
+    ref = O.filter_u8(small_image, 5, "ddf", p, dist, 4)
+    out, idx, st = gpu(V, small_image, 5, "ddf", p, dist, 4, "fp32", shape=shape)
+    V.set_tuned_shape(5, "ddf", dist, 0)
     assert_same(out, idx, ref, f"shape {shape}")
     assert st["overflow"] == 0
 
