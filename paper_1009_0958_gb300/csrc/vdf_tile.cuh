@@ -103,8 +103,17 @@ struct TileCfg {
     static constexpr size_t PLANE_BYTES = sizeof(PlaneT) * PBUF;
     static constexpr size_t HW_BYTES = sizeof(HwT) * TW * TH * NW;
     // two plane buffers (slice pipeline); FP64 reuses them for the per-window
-    // slots afterwards, FP32 writes each slot as soon as its aggregate is final
-    static constexpr size_t PLANES2_BYTES = (2 * PLANE_BYTES + 15) / 16 * 16;
+    // slots afterwards, FP32 writes each slot as soon as its aggregate is final.
+    // FP32 DDF 5x5 with raw slots takes one plane buffer (the slices then take
+    // two barriers each, mirrored row first) where that, and only that, lets
+    // two blocks share an SM (24x12 and 32x8)
+    static constexpr bool TWO_CTA_REGS = 2 * NT * (R == 1 ? 48 : 64) <= 65536;
+    static constexpr size_t FIXED_BYTES = PIX_BYTES + AUX_BYTES + KEY_BYTES + HW_BYTES;
+    static constexpr size_t PLANE1_BYTES = (PLANE_BYTES + 15) / 16 * 16, PLANE2_BYTES = (2 * PLANE_BYTES + 15) / 16 * 16;
+    static constexpr bool PB1 = !FP64 && SQ < 0 && FILTER == DDF && R == 2 && TWO_CTA_REGS &&
+                                2 * (FIXED_BYTES + PLANE2_BYTES + 1024) > 228 * 1024 &&
+                                2 * (FIXED_BYTES + PLANE1_BYTES + 1024) <= 228 * 1024;
+    static constexpr size_t PLANES2_BYTES = PB1 ? PLANE1_BYTES : PLANE2_BYTES;
     static constexpr size_t HW_OFFSET = FP64 ? 0 : PLANES2_BYTES;
     static constexpr size_t UNION_BYTES =
         FP64 ? (2 * PLANE_BYTES > HW_BYTES ? 2 * PLANE_BYTES : HW_BYTES) : PLANES2_BYTES + HW_BYTES;
@@ -114,8 +123,7 @@ struct TileCfg {
     // SM's 228 KB of shared memory (1 KB reserved per CTA) with at least 48
     // registers per thread (64 for 5x5, whose slice pipeline spills below
     // that), so one CTA's barrier waits overlap the other's work
-    static constexpr int MINB =
-        (2 * (SMEM + 1024) <= 228 * 1024 && 2 * NT * (R == 1 ? 48 : 64) <= 65536) ? 2 : 1;
+    static constexpr int MINB = (2 * (SMEM + 1024) <= 228 * 1024 && TWO_CTA_REGS) ? 2 : 1;
 };
 
 // ------------------------------------------------------------ scores ------
@@ -534,6 +542,40 @@ __device__ __forceinline__ void vstep32(typename C::PlaneT (*st)[C::W], const ty
     }
 }
 
+// The same for the arrival order of one plane buffer, mirrored row first:
+// 0, +1, -1, +2, -2, ..., +2R, -2R.  R = 2: st0 = H0 (+H-1 +H-2 +H-3),
+// st1 = H0+H1 (+H2 +H3), st2 = H-1+H0+H1 (+H-2), st3 = H-1+H0+H1+H2; 14 adds
+// per column, every aggregate a chain of 2R+1 values (depth 2R).
+template <class C, int DY, class Emit>
+__device__ __forceinline__ void vstep32_mf(typename C::PlaneT (*st)[C::W], const typename C::PlaneT *h, Emit &emit)
+{
+    static_assert(C::R == 2, "one plane buffer: 5x5 only");
+#pragma unroll
+    for (int x = 0; x < C::W; ++x) {
+        const int ex = x - C::R;
+        if constexpr (DY == 0) st[0][x] = h[x];
+        else if constexpr (DY == 1) st[1][x] = psum<C>(st[0][x], h[x]);
+        else if constexpr (DY == -1) {
+            st[2][x] = psum<C>(st[1][x], h[x]);
+            st[0][x] = psum<C>(st[0][x], h[x]);
+        } else if constexpr (DY == 2) {
+            st[3][x] = psum<C>(st[2][x], h[x]);
+            st[1][x] = psum<C>(st[1][x], h[x]);
+        } else if constexpr (DY == -2) {
+            emit(0, ex, psum<C>(st[3][x], h[x]));
+            st[2][x] = psum<C>(st[2][x], h[x]);
+            st[0][x] = psum<C>(st[0][x], h[x]);
+        } else if constexpr (DY == 3) {
+            emit(-1, ex, psum<C>(st[3][x], h[x]));
+            st[1][x] = psum<C>(st[1][x], h[x]);
+        } else if constexpr (DY == -3) {
+            emit(1, ex, psum<C>(st[2][x], h[x]));
+            st[0][x] = psum<C>(st[0][x], h[x]);
+        } else if constexpr (DY == 4) emit(-2, ex, psum<C>(st[1][x], h[x]));
+        else emit(2, ex, psum<C>(st[0][x], h[x]));
+    }
+}
+
 // One phase of the FP32 pipeline: the terms of slice D+1 (stored, and summed
 // for this thread's own row at once), the mirrored row -D of slice D (row 0
 // for D = 0), then a barrier.
@@ -546,6 +588,53 @@ __device__ __forceinline__ void phase32(const typename C::Pix *pix, const Aux *a
 {
     constexpr int R = C::R, W = C::W, NC = C::NC, PXW = C::PXW, CW = C::CW;
     using PT = typename C::PlaneT;
+    if constexpr (C::PB1) {
+        // one plane buffer: the mirrored row -D of slice D first, a barrier,
+        // then the terms of slice D+1 into the same buffer
+        if (tid < NC) {
+            PT g[4 * R + 1], h[W];
+            if constexpr (D == 0) {
+                g[2 * R] = self_term;
+#pragma unroll
+                for (int dx = 1; dx <= 2 * R; ++dx) {
+                    g[2 * R + dx] = g0[dx - 1];
+                    g[2 * R - dx] = buf0[(dx - 1) * NC + tid - dx];
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k <= 4 * R; ++k) {
+                    const int dx = k - 2 * R;
+                    g[k] = buf0[(2 * R - dx) * NC + tid - D * CW + dx];
+                }
+            }
+            hsum32<C>(g, h);
+            vstep32_mf<C, -D>(st, h, emit);
+        }
+        if constexpr (D < 2 * R) {
+            constexpr int DYP = D + 1;
+            __syncthreads();   // slice D is read: the buffer takes slice D+1
+            if (tid < NC) {
+                PT g[4 * R + 1], h[W];
+                if (cy + DYP < C::CH) {
+#pragma unroll
+                    for (int k = 0; k <= 4 * R; ++k) {
+                        const int bi = (cy + DYP) * PXW + (cx + k);   // partner p + (DYP, k - 2R)
+                        Aux xb{};
+                        if constexpr (C::AUX) xb = aux[bi];
+                        g[k] = pair_term<C>(self_px, pix[bi], self_aux, xb, q);
+                        buf0[k * NC + tid] = g[k];
+                    }
+                    hsum32<C>(g, h);
+                } else {
+#pragma unroll
+                    for (int x = 0; x < W; ++x) h[x] = PT{};
+                }
+                vstep32_mf<C, DYP>(st, h, emit);
+            }
+        }
+        __syncthreads();
+        return;
+    }
     if (tid < NC) {
         if constexpr (D < 2 * R) {
             constexpr int DYP = D + 1;
@@ -1282,7 +1371,7 @@ __device__ __forceinline__ void tile_rest(const TileParams &prm, int b, int x0, 
     if constexpr (!C::FP64) {
         // FP32: each slot is written inside the pipeline once its aggregate is final
         all_slices32<C>(std::make_integer_sequence<int, 2 * R + 1>{}, prm, x0, y0, pix, aux, planes,
-                        planes + C::PBUF, hw, tid, cy, cx, self_px, self_aux, self_term, prm.q);
+                        C::PB1 ? planes : planes + C::PBUF, hw, tid, cy, cx, self_px, self_aux, self_term, prm.q);
     } else {
         PT acc[W][W];
 #pragma unroll
