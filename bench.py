@@ -384,9 +384,10 @@ def run_acwddf_workload(args):
     wst = vdf.alloc_workspace(M, N, "fp32", dev)
     stream = torch.cuda.current_stream(dev)
     K = args.steps
-    for win in (3, 5):
-        for dist in ("exact", "minimax", "rgb"):
-            vdf.autotune(ins[0], win, "ddf", 0.5, dist, reps=3)
+    tuned = {}
+    for win, dist in ((3, "exact"), (3, "minimax"), (3, "rgb"), (5, "exact")):
+        shape, _ = vdf.autotune_acwddf(ins[0], win, dist, 4, 2, 10.8, reps=3, workspace=wst)
+        tuned[f"{win}x{win} {dist}"] = vdf.tile_shapes()[shape]
 
     def timed(win, dist, prec, steps):
         def call(s):
@@ -427,7 +428,7 @@ def run_acwddf_workload(args):
             "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": "ACWDDF on the 1920x1080 frames of the DDF workload (sinusoid field + 12 "
                                    "rectangles, 10% impulses), 24 frames (149 MB) in rotation", "M": M, "N": N,
-                       "lambda": 2, "T": 10.8},
+                       "lambda": 2, "T": 10.8, "tuned_shapes": tuned},
             "cases": cases, "fp64_path": {"value": head["fp64_value"], "unit": UNIT},
             "speedup_vs_fp64": head["speedup_vs_fp64"], "gpu_launches": 2 * K, "roofline": roofline,
             "clocks": clk.summary()}

@@ -317,12 +317,20 @@ int vdf_filter_noalloc(const uint8_t *img, int M, int N, int win, int filter, do
  * that p's entry, vdf_get_tuned_shape_p(..., p) reads the entry used at
  * exponent p, vdf_get_tuned_shape reads the entry of the other exponents, and
  * vdf_set_tuned_shape sets them all.
+ * vdf_autotune_acwddf does the same for the ACWDDF (its arguments as
+ * vdf_filter_acwddf, with the FP32 precision): it times the ACWDDF kernel in
+ * every shape and records the fastest in an entry of its own, which
+ * vdf_filter_acwddf reads (vdf_set_tuned_shape with filter VDF_DDF sets it
+ * too).  Window 7: VDF_E_UNSUPPORTED.
  */
 int vdf_num_tile_shapes(void);
 int vdf_tile_shape(int shape, int *tile_w, int *tile_h);
 int vdf_autotune(const uint8_t *img, int M, int N, int win, int filter, double p, int dist_mode, int minimax_q,
                  uint8_t *out, int8_t *index_out, void *workspace, size_t workspace_bytes, int reps, void *stream,
                  int *best_shape, float *best_ms);
+int vdf_autotune_acwddf(const uint8_t *img, int M, int N, int win, int dist_mode, int minimax_q, int lambda,
+                        double T, uint8_t *out, int8_t *index_out, void *workspace, size_t workspace_bytes, int reps,
+                        void *stream, int *best_shape, float *best_ms);
 int vdf_get_tuned_shape(int win, int filter, int dist_mode);
 int vdf_get_tuned_shape_p(int win, int filter, int dist_mode, double p);
 int vdf_set_tuned_shape(int win, int filter, int dist_mode, int shape);

@@ -67,8 +67,9 @@ int recheck_blocks() { return num_sms() * 16; }
 // Tile shape of the FP32 kernel per (window, filter, distance mode, slot
 // kind): shape 0 until vdf_autotune or vdf_set_tuned_shape records another.
 // Kinds 1..3 are the score-slot kernels (DDF 5x5 at p = kind / 4), whose
-// best shape differs from the raw-slot kernels' of the same configuration.
-constexpr int kSlotKinds = 4;
+// best shape differs from the raw-slot kernels' of the same configuration;
+// kind 4 is the ACWDDF's kernel (its DDF entry).
+constexpr int kSlotKinds = 5, kAcwKind = 4;
 std::mutex g_tune_mutex;
 int g_tuned[2][3][3][kSlotKinds] = {};
 
@@ -164,6 +165,32 @@ int vdf::check_args_no_workspace(const uint8_t *img, int M, int N, int win, int 
     if (!valid_common(M, N, win, filter, p, dist_mode, minimax_q, VDF_PREC_FP32_RECHECK)) return VDF_E_INVALID;
     return check_filter_args(img, M, N, win, filter, p, dist_mode, minimax_q, VDF_PREC_FP64, out, index_out, nullptr,
                              nullptr, 0);
+}
+
+// The FP32 ACWDDF in one tile shape: counter reset, tile kernel, FP64
+// recheck of the listed pixels (arguments already checked).
+static cudaError_t acw_pass_shape(const vdf::TileParams &prm, const uint8_t *img, int M, int N, int win,
+                                  int dist_mode, int minimax_q, int lambda, double T, int shape, cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(prm.recheck_ctr, 0, vdf::kCounterBlockBytes, st);
+    if (e == cudaSuccess) e = vdf::run_fp32_acw(prm, win / 2, dist_mode, shape, st);
+    if (e == cudaSuccess) {
+        vdf::RecheckParams rp{};
+        rp.img = img;
+        rp.out = prm.out;
+        rp.idx = prm.idx;
+        rp.list = prm.recheck_list;
+        rp.ctr = prm.recheck_ctr;
+        rp.cap = prm.recheck_cap;
+        rp.M = M;
+        rp.N = N;
+        rp.p = 0.5;
+        rp.q = minimax_q;
+        rp.lam = lambda;
+        rp.T = T;
+        e = vdf::run_recheck_acw(rp, win / 2, dist_mode, recheck_blocks(), st);
+    }
+    return e;
 }
 
 extern "C" {
@@ -323,26 +350,10 @@ int vdf_filter_acwddf(const uint8_t *img, int M, int N, int win, int dist_mode, 
     prm.lam = lambda;
     prm.T = T;
     if (precision == VDF_PREC_FP64) return cuda_fail(vdf::run_fp64_acw(prm, win / 2, dist_mode, st));
-    cudaError_t e = cudaMemsetAsync(prm.recheck_ctr, 0, vdf::kCounterBlockBytes, st);
-    if (e == cudaSuccess) e = vdf::run_fp32_acw(prm, win / 2, dist_mode, tuned_shape(win, VDF_DDF, dist_mode), st);
-    if (e == cudaSuccess) {
-        vdf::RecheckParams rp{};
-        rp.img = img;
-        rp.out = out;
-        rp.idx = index_out;
-        rp.list = prm.recheck_list;
-        rp.ctr = prm.recheck_ctr;
-        rp.cap = prm.recheck_cap;
-        rp.M = M;
-        rp.N = N;
-        rp.p = 0.5;
-        rp.q = minimax_q;
-        rp.lam = lambda;
-        rp.T = T;
-        e = vdf::run_recheck_acw(rp, win / 2, dist_mode, recheck_blocks(), st);
-    }
-    return cuda_fail(e);
+    return cuda_fail(acw_pass_shape(prm, img, M, N, win, dist_mode, minimax_q, lambda, T,
+                                    tuned_shape(win, VDF_DDF, dist_mode, kAcwKind), st));
 }
+
 
 int vdf_filter(const uint8_t *img, int M, int N, int win, int filter, double p, int dist_mode, int minimax_q,
                int precision, uint8_t *out, int8_t *index_out, double *agg_out, void *workspace,
@@ -562,6 +573,52 @@ int vdf_autotune(const uint8_t *img, int M, int N, int win, int filter, double p
     if (best_shape) *best_shape = bs;
     if (best_ms) *best_ms = best;
     return rc;
+}
+
+int vdf_autotune_acwddf(const uint8_t *img, int M, int N, int win, int dist_mode, int minimax_q, int lambda,
+                        double T, uint8_t *out, int8_t *index_out, void *workspace, size_t workspace_bytes, int reps,
+                        void *stream, int *best_shape, float *best_ms)
+{
+    int rc = check_filter_args(img, M, N, win, VDF_DDF, 0.5, dist_mode, minimax_q, VDF_PREC_FP32_RECHECK, out,
+                               index_out, nullptr, workspace, workspace_bytes);
+    if (rc != VDF_OK) return rc;
+    if (win == 7) return VDF_E_UNSUPPORTED;
+    const int d1 = (win * win + 1) / 2;
+    if (lambda < 1 || lambda > d1 - 2 || !std::isfinite(T)) return VDF_E_INVALID;
+    if (reps < 1) reps = 1;
+    cudaStream_t st = (cudaStream_t)stream;
+    vdf::TileParams prm = tile_params(img, M, N, 0.5, minimax_q, out, index_out, nullptr, workspace);
+    prm.lam = lambda;
+    prm.T = T;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    float best = 3.4e38f;
+    int bs = 0;
+    for (int s = 0; s < vdf::kNumShapes32 && e == cudaSuccess; ++s) {
+        e = acw_pass_shape(prm, img, M, N, win, dist_mode, minimax_q, lambda, T, s, st);
+        if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+        for (int r = 0; r < reps && e == cudaSuccess; ++r)
+            e = acw_pass_shape(prm, img, M, N, win, dist_mode, minimax_q, lambda, T, s, st);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess && ms / reps < best) {
+            best = ms / reps;
+            bs = s;
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (e != cudaSuccess) return cuda_fail(e);
+    record_tuned_shape(win, VDF_DDF, dist_mode, kAcwKind, bs);
+    // leave a complete result in out / index_out
+    e = acw_pass_shape(prm, img, M, N, win, dist_mode, minimax_q, lambda, T, bs, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (best_shape) *best_shape = bs;
+    if (best_ms) *best_ms = best;
+    return cuda_fail(e);
 }
 
 int vdf_debug_fp32_scores(const uint8_t *img, int M, int N, int win, int filter, double p, int dist_mode,

@@ -343,11 +343,12 @@ def _tune_fns(L):
     P, i, d, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
     if L.vdf_autotune.argtypes is None:
         L.vdf_autotune.argtypes = [P, i, i, i, i, d, i, i, P, P, P, sz, i, P, P, P]
+        L.vdf_autotune_acwddf.argtypes = [P, i, i, i, i, i, i, d, P, P, P, sz, i, P, P, P]
         L.vdf_tile_shape.argtypes = [i, P, P]
         L.vdf_get_tuned_shape.argtypes = [i, i, i]
         L.vdf_get_tuned_shape_p.argtypes = [i, i, i, d]
         L.vdf_set_tuned_shape.argtypes = [i, i, i, i]
-        for f in ("vdf_autotune", "vdf_tile_shape", "vdf_get_tuned_shape", "vdf_get_tuned_shape_p",
+        for f in ("vdf_autotune", "vdf_autotune_acwddf", "vdf_tile_shape", "vdf_get_tuned_shape", "vdf_get_tuned_shape_p",
                   "vdf_set_tuned_shape", "vdf_num_tile_shapes"):
             getattr(L, f).restype = i
     return L
@@ -377,6 +378,23 @@ def autotune(img: torch.Tensor, win=5, filter="ddf", p=0.25, dist="exact", q=4, 
     s, ms = ctypes.c_int(), ctypes.c_float()
     _check(L.vdf_autotune(_ptr(img), M, N, win, _code(FILTERS, filter), float(p), _code(DISTS, dist), q, _ptr(out),
                           _ptr(idx), wp, wn, reps, _stream(stream), ctypes.byref(s), ctypes.byref(ms)))
+    return s.value, ms.value
+
+
+def autotune_acwddf(img: torch.Tensor, win: int, dist: str = "exact", q: int = 4, lam: int = 2, T: float = 10.8,
+                    reps: int = 3, workspace=None, stream=None):
+    """Times the FP32 ACWDDF (Eq. (9)) in every tile shape on ``img`` and records the
+    fastest for vdf_filter_acwddf.  Returns (shape, ms)."""
+    L = _tune_fns(lib())
+    img = img.contiguous()
+    M, N = int(img.shape[0]), int(img.shape[1])
+    out = torch.empty_like(img)
+    idx = torch.empty((M, N), dtype=torch.int8, device=img.device)
+    ws = workspace if workspace is not None else alloc_workspace(M, N, "fp32", img.device)
+    wp, wn = _aligned(ws)
+    s, ms = ctypes.c_int(), ctypes.c_float()
+    _check(L.vdf_autotune_acwddf(_ptr(img), M, N, win, _code(DISTS, dist), q, int(lam), float(T), _ptr(out), _ptr(idx),
+                                 wp, wn, reps, _stream(stream), ctypes.byref(s), ctypes.byref(ms)))
     return s.value, ms.value
 
 

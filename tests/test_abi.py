@@ -137,6 +137,18 @@ def test_tuned_shape_table_kinds(L):
             L.vdf_set_tuned_shape(5, 1, dist, 0)
 
 
+def test_autotune_acwddf_argument_checks(L, B):
+    """Rejected before any launch: a null image, a missing workspace, a bad
+    smoothing level."""
+    P = ctypes.c_void_p
+    L.vdf_autotune_acwddf.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                      ctypes.c_int, ctypes.c_double, P, P, P, ctypes.c_size_t, ctypes.c_int, P, P, P]
+    L.vdf_autotune_acwddf.restype = ctypes.c_int
+    img, out = B
+    assert L.vdf_autotune_acwddf(None, 8, 8, 3, 0, 4, 2, 10.8, out, None, None, 0, 1, None, None, None) == -1
+    assert L.vdf_autotune_acwddf(img, 8, 8, 3, 0, 4, 2, 10.8, out, None, None, 0, 1, None, None, None) == -5
+
+
 def test_aliasing_and_workspace_checks(L, B):
     p = B[0]
     assert L.vdf_filter(p, 8, 8, 3, 0, 0.5, 0, 4, 0, p, None, None, None, 0, None) == -1      # out == img

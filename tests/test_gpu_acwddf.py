@@ -106,6 +106,23 @@ def test_every_tile_shape(V):
         V.set_tuned_shape(5, "ddf", "exact", 0)
 
 
+@pytest.mark.parametrize("win,dist", [(3, "exact"), (5, "exact"), (3, "minimax")])
+def test_autotune_acwddf(V, O, win, dist):
+    """The ACWDDF's own tile-shape autotuner: a shape in range, a valid time,
+    and later calls (in the recorded shape) equal to the oracle."""
+    from paper_1009_0958_gb300 import synth
+    img = synth.make_image(130, 170, 31, 0.15, rectangles=8)[1]
+    x = torch.from_numpy(img).cuda()
+    try:
+        shape, ms = V.autotune_acwddf(x, win, dist, 4, 2, 10.8, reps=2)
+        assert 0 <= shape < len(V.tile_shapes()) and ms > 0
+        o, i = V.filter_acwddf(x, win, dist, 4, 2, 10.8, precision="fp32")
+        ref = O.filter_acwddf(img, win, dist, 4, 2, 10.8)
+        assert np.array_equal(i.cpu().numpy(), ref["idx"]) and np.array_equal(o.cpu().numpy(), ref["out"])
+    finally:
+        V.set_tuned_shape(win, "ddf", dist, 0)
+
+
 def test_bad_arguments(V):
     x = torch.zeros((8, 8, 3), dtype=torch.uint8, device="cuda")
     for lam in (0, 4):
