@@ -250,9 +250,9 @@ static int fp32_pass_norm(const uint8_t *img, int M, int N, int win, int filter,
                           void *stream, int norm)
 {
     if (!valid_common(M, N, win, filter, p, dist_mode, minimax_q, VDF_PREC_FP32_RECHECK)) return VDF_E_INVALID;
+    const int shape = tuned_shape(win, filter, dist_mode, slot_kind(win, filter, dist_mode, norm, p));
     return fp32_pass_shape(img, M, N, win, filter, p, dist_mode, minimax_q, out, index_out, workspace,
-                           workspace_bytes, tuned_shape(win, filter, dist_mode, slot_kind(win, filter, dist_mode, norm, p)),
-                           stream, norm);
+                           workspace_bytes, shape, stream, norm);
 }
 
 static int fp64_recheck_norm(const uint8_t *img, int M, int N, int win, int filter, double p, int dist_mode,

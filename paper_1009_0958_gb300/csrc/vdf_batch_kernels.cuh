@@ -19,7 +19,8 @@ struct BatchDesc {
     int tiles_x;
     int tile_base;   // first work item of this image within its group
     int pix_base;    // first batch pixel offset of this image (ascending over the descriptor array)
-    int cfg;         // ((win/2 - 1) * 2 + filter) * kNumShapes32 + shape; DDF 5x5 at p = a/4: kScoreCfg0 + (a-1) * kNumShapes32 + shape
+    int cfg;         // ((win/2 - 1) * 2 + filter) * kNumShapes32 + shape, or for the
+                     // DDF 5x5 at p = a/4: kScoreCfg0 + (a - 1) * kNumShapes32 + shape
     double p;
 };
 

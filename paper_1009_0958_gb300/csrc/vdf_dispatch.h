@@ -18,7 +18,8 @@ constexpr int kNumShapes32 = 4;
 // 28x16 gives a 640-thread block (a multiple of 128), which leaves 96
 // registers per thread for DDF 5x5 instead of the 80 of 32x16's 736.  24x12
 // (448 threads) fits two blocks per SM where the slots are single values
-// (BVDF, VMF, and the DDF's score slots at p = 1/4).
+// (BVDF, VMF, and the DDF's score slots at p = 1/4, 1/2, 3/4), and for the
+// DDF's raw slots with one plane buffer.
 inline constexpr TileShape kShapes32[kNumShapes32] = {{32, 16}, {32, 8}, {24, 12}, {28, 16}};
 cudaError_t run_fp32(const TileParams &prm, int R, int filter, int dist, int shape, cudaStream_t st);
 // The exponent a of the FP32 kernel's score slots (TileCfg::SQ: each slot

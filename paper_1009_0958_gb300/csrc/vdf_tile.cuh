@@ -109,7 +109,8 @@ struct TileCfg {
     // two blocks share an SM (24x12 and 32x8)
     static constexpr bool TWO_CTA_REGS = 2 * NT * (R == 1 ? 48 : 64) <= 65536;
     static constexpr size_t FIXED_BYTES = PIX_BYTES + AUX_BYTES + KEY_BYTES + HW_BYTES;
-    static constexpr size_t PLANE1_BYTES = (PLANE_BYTES + 15) / 16 * 16, PLANE2_BYTES = (2 * PLANE_BYTES + 15) / 16 * 16;
+    static constexpr size_t PLANE1_BYTES = (PLANE_BYTES + 15) / 16 * 16;
+    static constexpr size_t PLANE2_BYTES = (2 * PLANE_BYTES + 15) / 16 * 16;
     static constexpr bool PB1 = !FP64 && SQ < 0 && FILTER == DDF && R == 2 && TWO_CTA_REGS &&
                                 2 * (FIXED_BYTES + PLANE2_BYTES + 1024) > 228 * 1024 &&
                                 2 * (FIXED_BYTES + PLANE1_BYTES + 1024) <= 228 * 1024;
