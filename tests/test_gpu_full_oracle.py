@@ -120,11 +120,12 @@ def test_tile_shapes_methods_1_and_2(V, O, small_image, shape, win, filter, p, d
 
 
 @pytest.mark.parametrize("shape", [0, 1, 2, 3])
-@pytest.mark.parametrize("p", [0.25, 0.5, 0.75])
+@pytest.mark.parametrize("p", [0.25, 0.5, 0.75, 0.3])
 @pytest.mark.parametrize("dist", ["exact", "rgb"])
 def test_score_slot_kernels_every_shape(V, O, small_image, shape, p, dist):
     """The DDF 5x5 at p = 1/4, 1/2 and 3/4 runs with score slots (Omega^4 per
-    slot) in every tile shape: every pixel equals the oracle."""
+    slot), at p = 0.3 with raw slots (one plane buffer at 24x12 and 32x8), in
+    every tile shape: every pixel equals the oracle."""
     ref = O.filter_u8(small_image, 5, "ddf", p, dist, 4)
     out, idx, st = gpu(V, small_image, 5, "ddf", p, dist, 4, "fp32", shape=shape)
     V.set_tuned_shape(5, "ddf", dist, 0)

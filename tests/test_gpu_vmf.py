@@ -141,6 +141,25 @@ def test_vmf_every_tile_shape_and_order2_equals_ddf_p0(V):
     assert torch.equal(v2[0], d0[0]) and torch.equal(v2[1], d0[1])
 
 
+@pytest.mark.parametrize("order", [1, "inf"])
+@pytest.mark.parametrize("p", [0.25, 0.3])
+def test_ddf_orders_every_tile_shape(V, O, order, p):
+    """The DDF with the Minkowski distance term of order 1 or infinity keeps
+    raw slots (one plane buffer at 24x12 and 32x8): every FP32 tile shape
+    equals the oracle on every pixel."""
+    from paper_1009_0958_gb300 import synth
+    img = synth.make_image(70, 101, 3, 0.2, rectangles=10)[1]
+    ref = O.filter_u8(img, 5, "ddf", p, "exact", 4, order=order)
+    try:
+        for s in range(len(V.tile_shapes())):
+            V.set_tuned_shape(5, "ddf", "exact", s)
+            out, idx, _, (rc, ov) = run(V, img, 5, "ddf", p, order, "fp32")
+            assert ov == 0
+            assert np.array_equal(idx, ref["idx"]) and np.array_equal(out, ref["out"]), f"shape {s}"
+    finally:
+        V.set_tuned_shape(5, "ddf", "exact", 0)
+
+
 def test_unsupported_combinations(V):
     x = torch.zeros((8, 8, 3), dtype=torch.uint8, device="cuda")
     with pytest.raises(V.VdfError):
